@@ -1,0 +1,145 @@
+/*
+ * ccgf.h - C ABI of the GB300 periodic coupled-cluster Green's function library.
+ *
+ * The library computes the k-point CCGF of the paper (Eq. 9),
+ *   G+_pq(k,w) = <Phi0|(1+Lambda) a_bar_{pk} [w - (H_bar - E) + i eta]^-1 a_bar+_{qk} |Phi0>,
+ *   G-_pq(k,w) = <Phi0|(1+Lambda) a_bar+_{qk} [w + (H_bar - E) - i eta]^-1 a_bar_{pk} |Phi0>,
+ * with the EOM-CCSD ansatz of Eq. 8 (1h + 2h1p for the removal part,
+ * 1p + 2p1h for the addition part): the shifted linear systems of Eq. 6 are
+ * solved by batched GMRES whose operator is the EOM-IP / EA-CCSD
+ * similarity-transformed Hamiltonian (the sigma vector), and the solutions are
+ * contracted with the left vectors as in Eq. 7.
+ *
+ * Conventions shared by every call
+ *   - Complex numbers are interleaved pairs of double (re, im): a "complex
+ *     array of n elements" is 2n doubles, 16-byte aligned.
+ *   - k index = (k1*n2 + k2)*n3 + k3 on the (n1, n2, n3) mesh; momentum
+ *     addition is modulo each mesh dimension.
+ *   - Orbitals per k are ordered occupied first (nocc), then virtual (nvir);
+ *     nmo = nocc + nvir. The reference Fock matrix is diag(mo_energy).
+ *   - Closed-shell (restricted) reference; G_pq is the alpha-alpha block.
+ *   - EOM vectors at total momentum K, spin-adapted:
+ *       IP: r1[i] (nocc), then r2[ki][kj][i][j][a] with k_a = ki + kj - K;
+ *       EA: r1[a] (nvir), then r2[kj][ka][j][a][b] with k_b = K + kj - ka.
+ *     dim_ip = nocc + nk^2 nocc^2 nvir, dim_ea = nvir + nk^2 nocc nvir^2.
+ *   - Every call is stream-ordered on the caller's CUDA stream (cudaStream_t
+ *     passed as void*; NULL = the legacy default stream). Only ccgf_solve_gf
+ *     synchronises (once per GMRES cycle, to read convergence flags).
+ *   - Errors are returned as status codes; nothing aborts, throws or traps.
+ *     ccgf_last_error() gives a message for the last failing call on this
+ *     thread. One handle per host thread.
+ */
+#ifndef CCGF_H
+#define CCGF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CCGF_OK = 0,
+    CCGF_NOT_CONVERGED = 1,      /* warning: outputs written, some residuals above tol */
+    CCGF_ERR_INVALID_ARG = -1,
+    CCGF_ERR_OOM = -2,
+    CCGF_ERR_CUDA = -3,
+    CCGF_ERR_NAN = -4,
+    CCGF_ERR_TIMEOUT = -5
+} ccgf_status;
+
+typedef enum {
+    CCGF_FP64 = 0,       /* plain form: every step in FP64 */
+    CCGF_FP32 = 1        /* sigma contractions in FP32 (FP32 accumulate) inside FP64 refinement */
+} ccgf_precision;
+
+typedef enum { CCGF_SECTOR_IP = 1, CCGF_SECTOR_EA = 2, CCGF_SECTOR_BOTH = 3 } ccgf_sector;
+
+/* The problem of the paper's k-point CCGF section: orbital energies, integrals,
+ * ground-state amplitudes and Lambda. All pointers are borrowed for the call
+ * and copied; they are host pointers unless inputs_on_device != 0.          */
+typedef struct {
+    int kmesh[3];
+    int nocc, nvir, naux;
+    const double *mo_energy;  /* real [nk][nmo]                                           */
+    const double *L;          /* complex [nk][nk][naux][nmo][nmo]: (p k1 q k2|r k3 s k4) =
+                                 sum_Q L[k1,k2,Q,p,q] L[k3,k4,Q,r,s] if k1+k3 = k2+k4     */
+    const double *t1;         /* complex [nk][nocc][nvir]                                 */
+    const double *t2;         /* complex [nk][nk][nk][nocc][nocc][nvir][nvir],
+                                 t2[ki,kj,ka][i,j,a,b], k_b = ki + kj - ka                */
+    const double *l1;         /* complex, layout of t1; NULL => conj(t1)                  */
+    const double *l2;         /* complex, layout of t2; NULL => conj(t2)                  */
+    int inputs_on_device;
+} ccgf_system;
+
+typedef struct {
+    ccgf_precision prec;      /* arithmetic of the inner sigma (see ccgf_precision)       */
+    double tol;               /* relative residual ||b - M x|| / ||b|| per right-hand side */
+    int restart_m;            /* GMRES restart length                                      */
+    int max_iter;             /* cap on inner iterations per right-hand side              */
+    int max_refine;           /* cap on FP64 true-residual checks (refinement cycles)      */
+    int omega_chunk;          /* frequencies solved together per (sector, K) batch         */
+    double device_wait_timeout_ms; /* reserved for bounded device waits                   */
+} ccgf_options;
+
+typedef struct {
+    long long rhs_solved;       /* right-hand sides solved                                */
+    long long inner_iterations; /* sum over batches of GMRES iterations (batch-parallel)  */
+    long long fp64_sigma_calls; /* FP64 sigma batches (true-residual recomputes)          */
+    long long lowp_sigma_calls; /* FP32 sigma batches                                     */
+    double max_rel_residual;    /* largest final true relative residual                   */
+    double sigma_ms;            /* device time in sigma (CUDA events)                     */
+    double total_ms;            /* device time of the whole solve                         */
+    long long kernel_launches;  /* kernels launched by the solve                          */
+} ccgf_stats;
+
+typedef struct ccgf_handle ccgf_handle;
+
+/* Default options: FP64, tol 1e-10, restart 30, max_iter 2000, max_refine 20, omega_chunk 1. */
+void ccgf_default_options(ccgf_options *opt);
+
+/* Build the similarity-transformed Hamiltonian blocks (Eq. 5) for the EOM-CCSD
+ * sigma vectors: T1-dressed integrals, F_oo, F_vv, F_ov and the W blocks, all in
+ * FP64 (plus FP32 copies), in GEMM-ready layouts; also the RHS / left-vector
+ * ingredients (T, Lambda). The handle owns all device memory it allocates.
+ * Errors: INVALID_ARG (sizes, NULL), OOM (cudaMalloc), CUDA, NAN (non-finite input). */
+ccgf_status ccgf_build_intermediates(const ccgf_system *sys, const ccgf_options *opt,
+                                     void *stream, ccgf_handle **out);
+
+ccgf_status ccgf_dims(const ccgf_handle *h, int *nk, int *nocc, int *nvir,
+                      long long *dim_ip, long long *dim_ea);
+
+/* y = A_IP x (Eq. 8, removal part): the connected EOM-IP-CCSD operator H_bar - E
+ * on nvec vectors at total momentum kshift. x, y: device complex [nvec][dim_ip],
+ * caller-owned, must not alias. prec selects FP64 or FP32 arithmetic (inputs and
+ * outputs stay FP64). Errors: INVALID_ARG (kshift, nvec, NULL), OOM (workspace), CUDA. */
+ccgf_status ccgf_sigma_ip(ccgf_handle *h, int kshift, long long nvec, const double *x,
+                          double *y, ccgf_precision prec, void *stream);
+
+/* y = A_EA x (Eq. 8, addition part), as ccgf_sigma_ip with dim_ea. */
+ccgf_status ccgf_sigma_ea(ccgf_handle *h, int kshift, long long nvec, const double *x,
+                          double *y, ccgf_precision prec, void *stream);
+
+/* Right-hand side b_p = P a_bar_p |Phi0> (IP) or b_q = P a_bar+_q |Phi0> (EA) and
+ * left vector e_q = <Phi0|(1+Lambda) a_bar+_q|mu> (IP) or e_p = <..|a_bar_p|mu> (EA)
+ * for orbital p at momentum K (Eq. 6-7); out: device complex [dim]. */
+ccgf_status ccgf_rhs(ccgf_handle *h, int sector, int K, int p, double *out, void *stream);
+ccgf_status ccgf_left(ccgf_handle *h, int sector, int K, int p, double *out, void *stream);
+
+/* G_pq(k,w) = G+ + G- (Eq. 9) for all k, all p, q and the nomega frequencies,
+ * sectors = CCGF_SECTOR_IP / EA / BOTH (the other part is left out of the sum).
+ * IP: (w - i eta + A_IP) X_p = b_p, G-[p,q] = e_q . X_p;
+ * EA: (w + i eta - A_EA) Y_q = b_q, G+[p,q] = e_p . Y_q.
+ * G_out: complex [nk][nomega][nmo][nmo], caller-owned, host or device memory
+ * (G_on_device). omega: host array. Returns NOT_CONVERGED (G still written) when
+ * some right-hand side missed opt->tol within the caps. stats may be NULL. */
+ccgf_status ccgf_solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omega,
+                          double eta, const ccgf_options *opt, double *G_out, int G_on_device,
+                          ccgf_stats *stats, void *stream);
+
+void ccgf_destroy(ccgf_handle *h);
+const char *ccgf_status_string(ccgf_status s);
+const char *ccgf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CCGF_H */

@@ -1,0 +1,191 @@
+// extern "C" entry points of the CCGF library (see include/ccgf.h).
+#include "ccgf_internal.h"
+#include <cmath>
+#include <new>
+
+namespace {
+
+ccgf_status copy_in(DBuf<double2> &dst, const double *src, i64 n, bool on_device, cudaStream_t st) {
+    CCGF_TRY(dalloc(dst, n));
+    CCGF_CUDA_TRY(cudaMemcpyAsync(dst.p, src, sizeof(double2) * n, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    return CCGF_OK;
+}
+
+__global__ void conj_kernel(const double2 *a, double2 *b, i64 n) {
+    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) b[i] = make_double2(a[i].x, -a[i].y);
+}
+
+void destroy(ccgf_handle *h) {
+    if (!h) return;
+    free_plans(h);
+    dfree(h->t1);
+    dfree(h->t2);
+    dfree(h->l1);
+    dfree(h->l2);
+    dfree(h->L);
+    dfree(h->eps);
+    dfree(h->kadd_d);
+    dfree(h->ksub_d);
+    for (int b = 0; b < NBUF; ++b) {
+        dfree(h->W[b]);
+        dfree(h->Wf[b]);
+    }
+    dfree(h->scratch);
+    dfree(h->scratch_f);
+    dfree(h->yf);
+    delete h;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ccgf_default_options(ccgf_options *opt) {
+    if (!opt) return;
+    opt->prec = CCGF_FP64;
+    opt->tol = 1e-10;
+    opt->restart_m = 30;
+    opt->max_iter = 2000;
+    opt->max_refine = 20;
+    opt->omega_chunk = 1;
+    opt->device_wait_timeout_ms = 1000.0;
+}
+
+const char *ccgf_status_string(ccgf_status s) {
+    switch (s) {
+        case CCGF_OK: return "ok";
+        case CCGF_NOT_CONVERGED: return "not converged (outputs written)";
+        case CCGF_ERR_INVALID_ARG: return "invalid argument";
+        case CCGF_ERR_OOM: return "out of device memory";
+        case CCGF_ERR_CUDA: return "CUDA error";
+        case CCGF_ERR_NAN: return "non-finite input";
+        case CCGF_ERR_TIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+ccgf_status ccgf_build_intermediates(const ccgf_system *sys, const ccgf_options *opt, void *stream, ccgf_handle **out) {
+    (void)opt;
+    if (!sys || !out) { set_last_error("NULL system or output pointer"); return CCGF_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (sys->kmesh[0] < 1 || sys->kmesh[1] < 1 || sys->kmesh[2] < 1 || sys->nocc < 1 || sys->nvir < 1 || sys->naux < 1) {
+        set_last_error("kmesh, nocc, nvir and naux must be >= 1");
+        return CCGF_ERR_INVALID_ARG;
+    }
+    if (!sys->mo_energy || !sys->L || !sys->t1 || !sys->t2) { set_last_error("NULL input array"); return CCGF_ERR_INVALID_ARG; }
+    ccgf_handle *h = new (std::nothrow) ccgf_handle();
+    if (!h) { set_last_error("host allocation failed"); return CCGF_ERR_OOM; }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaGetDevice(&h->device);
+    h->km.init(sys->kmesh);
+    h->nk = h->km.nk;
+    h->o = sys->nocc;
+    h->v = sys->nvir;
+    h->n = sys->nocc + sys->nvir;
+    h->naux = sys->naux;
+    const i64 nk = h->nk, o = h->o, v = h->v, n = h->n;
+    h->dim_ip = o + nk * nk * o * o * v;
+    h->dim_ea = v + nk * nk * o * v * v;
+    const bool dev = sys->inputs_on_device != 0;
+    ccgf_status s = CCGF_OK;
+    auto fail = [&](ccgf_status e) { destroy(h); return e; };
+    if ((s = copy_in(h->L, sys->L, nk * nk * h->naux * n * n, dev, st)) != CCGF_OK) return fail(s);
+    if ((s = copy_in(h->t1, sys->t1, nk * o * v, dev, st)) != CCGF_OK) return fail(s);
+    if ((s = copy_in(h->t2, sys->t2, nk * nk * nk * o * o * v * v, dev, st)) != CCGF_OK) return fail(s);
+    if ((s = dalloc(h->eps, nk * n)) != CCGF_OK) return fail(s);
+    if (cudaMemcpyAsync(h->eps.p, sys->mo_energy, sizeof(double) * nk * n, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        set_last_error("copy of mo_energy failed");
+        return fail(CCGF_ERR_CUDA);
+    }
+    if (sys->l1) {
+        if ((s = copy_in(h->l1, sys->l1, nk * o * v, dev, st)) != CCGF_OK) return fail(s);
+    } else {
+        if ((s = dalloc(h->l1, nk * o * v)) != CCGF_OK) return fail(s);
+        conj_kernel<<<256, 256, 0, st>>>(h->t1.p, h->l1.p, h->l1.n);
+    }
+    if (sys->l2) {
+        if ((s = copy_in(h->l2, sys->l2, h->t2.n, dev, st)) != CCGF_OK) return fail(s);
+    } else {
+        if ((s = dalloc(h->l2, h->t2.n)) != CCGF_OK) return fail(s);
+        conj_kernel<<<1024, 256, 0, st>>>(h->t2.p, h->l2.p, h->l2.n);
+    }
+    if ((s = build_intermediates(h, sys, st)) != CCGF_OK) return fail(s);
+    *out = h;
+    return CCGF_OK;
+}
+
+ccgf_status ccgf_dims(const ccgf_handle *h, int *nk, int *nocc, int *nvir, long long *dim_ip, long long *dim_ea) {
+    if (!h) { set_last_error("NULL handle"); return CCGF_ERR_INVALID_ARG; }
+    if (nk) *nk = h->nk;
+    if (nocc) *nocc = h->o;
+    if (nvir) *nvir = h->v;
+    if (dim_ip) *dim_ip = h->dim_ip;
+    if (dim_ea) *dim_ea = h->dim_ea;
+    return CCGF_OK;
+}
+
+static ccgf_status sigma_abi(ccgf_handle *h, int sector, int kshift, long long nvec, const double *x, double *y,
+                             ccgf_precision prec, void *stream) {
+    if (!h || !x || !y) { set_last_error("NULL handle or vector"); return CCGF_ERR_INVALID_ARG; }
+    if (kshift < 0 || kshift >= h->nk) { set_last_error("kshift out of range"); return CCGF_ERR_INVALID_ARG; }
+    if (nvec < 1 || nvec > 65536) { set_last_error("nvec must be in [1, 65536]"); return CCGF_ERR_INVALID_ARG; }
+    if (prec != CCGF_FP64 && prec != CCGF_FP32) { set_last_error("unknown precision"); return CCGF_ERR_INVALID_ARG; }
+    cudaStream_t st = (cudaStream_t)stream;
+    const i64 D = sector == CCGF_SECTOR_IP ? h->dim_ip : h->dim_ea;
+    const int nv = (int)nvec;
+    DBuf<double2> xt, yt;
+    CCGF_TRY(dalloc(xt, D * nv));
+    ccgf_status s = dalloc(yt, D * nv);
+    if (s != CCGF_OK) { dfree(xt); return s; }
+    launch_transpose_in((const double2 *)x, xt.p, D, nv, nv, st);
+    s = sigma_apply(h, sector, kshift, nv, xt.p, yt.p, prec, st);
+    if (s == CCGF_OK) launch_transpose_out(yt.p, (double2 *)y, D, nv, nv, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    dfree(xt);
+    dfree(yt);
+    if (s != CCGF_OK) return s;
+    if (e != cudaSuccess) { set_last_error(cudaGetErrorString(e)); return CCGF_ERR_CUDA; }
+    return CCGF_OK;
+}
+
+ccgf_status ccgf_sigma_ip(ccgf_handle *h, int kshift, long long nvec, const double *x, double *y, ccgf_precision prec, void *stream) {
+    return sigma_abi(h, CCGF_SECTOR_IP, kshift, nvec, x, y, prec, stream);
+}
+ccgf_status ccgf_sigma_ea(ccgf_handle *h, int kshift, long long nvec, const double *x, double *y, ccgf_precision prec, void *stream) {
+    return sigma_abi(h, CCGF_SECTOR_EA, kshift, nvec, x, y, prec, stream);
+}
+
+static ccgf_status vec_abi(ccgf_handle *h, int sector, int K, int p, double *out, void *stream, bool left) {
+    if (!h || !out) { set_last_error("NULL handle or output"); return CCGF_ERR_INVALID_ARG; }
+    if (sector != CCGF_SECTOR_IP && sector != CCGF_SECTOR_EA) { set_last_error("sector must be IP or EA"); return CCGF_ERR_INVALID_ARG; }
+    if (K < 0 || K >= h->nk || p < 0 || p >= h->n) { set_last_error("K or orbital out of range"); return CCGF_ERR_INVALID_ARG; }
+    cudaStream_t st = (cudaStream_t)stream;
+    ccgf_status s = left ? make_left(h, sector, K, p, (double2 *)out, 1, st) : make_rhs(h, sector, K, p, (double2 *)out, 1, st);
+    if (s != CCGF_OK) return s;
+    CCGF_CUDA_TRY(cudaStreamSynchronize(st));
+    return CCGF_OK;
+}
+ccgf_status ccgf_rhs(ccgf_handle *h, int sector, int K, int p, double *out, void *stream) { return vec_abi(h, sector, K, p, out, stream, false); }
+ccgf_status ccgf_left(ccgf_handle *h, int sector, int K, int p, double *out, void *stream) { return vec_abi(h, sector, K, p, out, stream, true); }
+
+ccgf_status ccgf_solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omega, double eta, const ccgf_options *opt,
+                          double *G_out, int G_on_device, ccgf_stats *stats, void *stream) {
+    if (!h || !omega || !G_out) { set_last_error("NULL handle, omega or output"); return CCGF_ERR_INVALID_ARG; }
+    if (sectors < 1 || sectors > 3 || nomega < 1) { set_last_error("sectors must be 1..3 and nomega >= 1"); return CCGF_ERR_INVALID_ARG; }
+    if (!(eta > 0.0) || !std::isfinite(eta)) { set_last_error("eta must be positive and finite"); return CCGF_ERR_INVALID_ARG; }
+    for (int w = 0; w < nomega; ++w)
+        if (!std::isfinite(omega[w])) { set_last_error("non-finite frequency"); return CCGF_ERR_NAN; }
+    ccgf_options o;
+    if (opt) o = *opt;
+    else ccgf_default_options(&o);
+    if (!(o.tol > 0.0) || o.restart_m < 2 || o.max_iter < 1 || o.max_refine < 1 || o.omega_chunk < 1) {
+        set_last_error("invalid options (tol > 0, restart_m >= 2, max_iter >= 1, max_refine >= 1, omega_chunk >= 1)");
+        return CCGF_ERR_INVALID_ARG;
+    }
+    if (o.prec != CCGF_FP64 && o.prec != CCGF_FP32) { set_last_error("unknown precision"); return CCGF_ERR_INVALID_ARG; }
+    return solve_gf(h, sectors, nomega, omega, eta, &o, G_out, G_on_device, stats, (cudaStream_t)stream);
+}
+
+void ccgf_destroy(ccgf_handle *h) { destroy(h); }
+
+}  // extern "C"

@@ -1,0 +1,155 @@
+// Internal declarations of the CCGF library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+#include "../../include/ccgf.h"
+
+typedef long long i64;
+
+// ----------------------------------------------------------------------------- errors
+void set_last_error(const std::string &msg);
+#define CCGF_CUDA_TRY(expr)                                                                    \
+    do {                                                                                       \
+        cudaError_t _e = (expr);                                                               \
+        if (_e != cudaSuccess) {                                                               \
+            set_last_error(std::string(#expr) + ": " + cudaGetErrorString(_e));                \
+            return _e == cudaErrorMemoryAllocation ? CCGF_ERR_OOM : CCGF_ERR_CUDA;             \
+        }                                                                                      \
+    } while (0)
+#define CCGF_TRY(expr)                                                                         \
+    do {                                                                                       \
+        ccgf_status _s = (expr);                                                               \
+        if (_s != CCGF_OK) return _s;                                                          \
+    } while (0)
+
+// ----------------------------------------------------------------------------- complex types
+template <typename R> struct cvec;
+template <> struct cvec<double> { typedef double2 T; };
+template <> struct cvec<float> { typedef float2 T; };
+
+// ----------------------------------------------------------------------------- device buffers
+template <typename T> struct DBuf {
+    T *p = nullptr;
+    i64 n = 0;
+};
+ccgf_status dalloc_bytes(void **p, size_t bytes);
+template <typename T> ccgf_status dalloc(DBuf<T> &b, i64 n) {
+    b.n = n;
+    return dalloc_bytes((void **)&b.p, (size_t)(n > 0 ? n : 1) * sizeof(T));
+}
+template <typename T> void dfree(DBuf<T> &b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.n = 0;
+}
+
+// ----------------------------------------------------------------------------- batched GEMM
+// C_b = alpha * sum_{r<nred} A_{b,r} B_{b,r} + beta * C_b,  complex, b < batch.
+// A_{b,r}[m,k] = A0[offA[b*nred+r] + m*rsA + k*csA], likewise B[k,n], C[m,n].
+struct GemmDesc {
+    int M, N, K, nred, batch;
+    i64 rsA, csA, rsB, csB, rsC, csC;
+    const i64 *offA, *offB, *offC;   // device offset tables
+    double2 alpha, beta;
+};
+template <typename R>
+void launch_zgemm(const GemmDesc &d, const typename cvec<R>::T *A, const typename cvec<R>::T *B,
+                  typename cvec<R>::T *C, cudaStream_t st);
+
+// ----------------------------------------------------------------------------- batched permute
+// C[offC[b] + sum_d i_d sC_d] = alpha * A[offA[b] + sum_d i_d sA_d] + beta * C[...]
+struct PermDesc {
+    int nd;
+    i64 dims[6];
+    i64 sA[6], sC[6];
+    i64 total;
+    int batch;
+    const i64 *offA, *offC;
+    double2 alpha, beta;
+};
+template <typename R>
+void launch_zpermute(const PermDesc &d, const typename cvec<R>::T *A, typename cvec<R>::T *C, cudaStream_t st);
+
+// ----------------------------------------------------------------------------- k-mesh
+struct KMeshH {
+    int n[3];
+    int nk;
+    std::vector<int> add, sub;   // add[a*nk+b] = a+b, sub[a*nk+b] = a-b
+    void init(const int kmesh[3]);
+    int a(int x, int y) const { return add[x * nk + y]; }
+    int s(int x, int y) const { return sub[x * nk + y]; }
+    int c(int k1, int k2, int k3) const { return a(s(k1, k2), k3); }   // k1 - k2 + k3
+};
+
+// ----------------------------------------------------------------------------- sigma plan
+// A sigma plan is a list of launches over fixed buffers: A operands are
+// intermediates (buffer ids below), B operands always live in the scratch arena
+// (the input vector is copied there first), C operands are the output or scratch.
+enum { STEP_GEMM = 0, STEP_PERM = 1, STEP_FOV_IP = 2, STEP_FOV_EA = 3 };
+struct SigmaStep {
+    int kind;
+    GemmDesc g;
+    PermDesc p;
+    int a_buf;         // GEMM: intermediate id (or BUF_SCRATCH); PERM: source (BUF_SCRATCH)
+    int c_buf;         // BUF_Y or BUF_SCRATCH
+    i64 offA_pos, offB_pos, offC_pos;   // positions in the plan's offset table
+};
+struct SigmaPlan {
+    int sector, K, nv;
+    std::vector<SigmaStep> steps;
+    DBuf<i64> offsets;
+    std::vector<i64> host_off;
+    i64 scratch_elems;
+    i64 seg[8];        // scratch segment offsets (complex elements)
+};
+
+enum {
+    BUF_Y = 0, BUF_SCRATCH,
+    BUF_FOO, BUF_FVV, BUF_FOV,
+    BUF_WVVVV, BUF_WVVVO, BUF_WOV3, BUF_UVOVV, BUF_UOOVV_EA, BUF_T2EA,
+    BUF_WOVOO, BUF_WOOOO, BUF_UOOOV, BUF_UOOVV_IP, BUF_T2IP,
+    NBUF
+};
+
+struct ccgf_handle {
+    int device;
+    KMeshH km;
+    int nk, o, v, n, naux;
+    i64 dim_ip, dim_ea;
+    // FP64 inputs kept on device
+    DBuf<double2> t1, t2, l1, l2, L;
+    DBuf<double> eps;
+    DBuf<int> kadd_d, ksub_d;   // momentum tables on device
+    // FP64 intermediates (GEMM-ready), FP32 copies below
+    DBuf<double2> W[NBUF];
+    DBuf<float2> Wf[NBUF];
+    i64 wov_seg;       // size of each of W1 | W2 | WN inside BUF_WOV3
+    // scratch arena for sigma (FP64 and FP32 variants) and the FP32 output
+    DBuf<double2> scratch;
+    DBuf<float2> scratch_f, yf;
+    // cached plans, index (sector-1)*nk + K, valid for plan_nv columns
+    std::vector<SigmaPlan *> plans;
+    int plan_nv = 0;
+    i64 launches = 0;
+};
+
+// build.cu
+ccgf_status build_intermediates(ccgf_handle *h, const ccgf_system *sys, cudaStream_t st);
+// sigma.cu
+ccgf_status sigma_apply(ccgf_handle *h, int sector, int K, int nv, const double2 *x, double2 *y,
+                        ccgf_precision prec, cudaStream_t st);
+void free_plans(ccgf_handle *h);
+// vectors.cu
+ccgf_status make_rhs(ccgf_handle *h, int sector, int K, int p, double2 *out, i64 ld, cudaStream_t st);
+ccgf_status make_left(ccgf_handle *h, int sector, int K, int p, double2 *out, i64 ld, cudaStream_t st);
+// transposes between [nvec][D] (ABI) and [D][nv] (internal)
+void launch_transpose_in(const double2 *x, double2 *xt, i64 D, int nvec, int nv, cudaStream_t st);
+void launch_transpose_out(const double2 *yt, double2 *y, i64 D, int nvec, int nv, cudaStream_t st);
+// solve.cu
+ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omega, double eta,
+                     const ccgf_options *opt, double *G_out, int G_on_device, ccgf_stats *stats,
+                     cudaStream_t st);
+
+inline i64 ceil_div(i64 a, i64 b) { return (a + b - 1) / b; }

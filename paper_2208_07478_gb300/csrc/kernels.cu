@@ -1,0 +1,231 @@
+// Generic device kernels: batched complex GEMM (FP64 / FP32 SIMT), batched strided
+// permute-add, layout transposes, plus small shared helpers of the library.
+#include "ccgf_internal.h"
+#include <mutex>
+
+static thread_local std::string g_last_error;
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+extern "C" const char *ccgf_last_error(void) { return g_last_error.c_str(); }
+
+ccgf_status dalloc_bytes(void **p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        set_last_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? CCGF_ERR_OOM : CCGF_ERR_CUDA;
+    }
+    return CCGF_OK;
+}
+
+void KMeshH::init(const int kmesh[3]) {
+    n[0] = kmesh[0];
+    n[1] = kmesh[1];
+    n[2] = kmesh[2];
+    nk = n[0] * n[1] * n[2];
+    add.assign(nk * nk, 0);
+    sub.assign(nk * nk, 0);
+    for (int x = 0; x < nk; ++x) {
+        int xv[3] = {x / (n[1] * n[2]), (x / n[2]) % n[1], x % n[2]};
+        for (int y = 0; y < nk; ++y) {
+            int yv[3] = {y / (n[1] * n[2]), (y / n[2]) % n[1], y % n[2]};
+            int sa[3], sd[3];
+            for (int d = 0; d < 3; ++d) {
+                sa[d] = (xv[d] + yv[d]) % n[d];
+                sd[d] = ((xv[d] - yv[d]) % n[d] + n[d]) % n[d];
+            }
+            add[x * nk + y] = (sa[0] * n[1] + sa[1]) * n[2] + sa[2];
+            sub[x * nk + y] = (sd[0] * n[1] + sd[1]) * n[2] + sd[2];
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------- complex helpers
+template <typename T> __device__ __forceinline__ T cz();
+template <> __device__ __forceinline__ double2 cz<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ float2 cz<float2>() { return make_float2(0.f, 0.f); }
+
+template <typename T, typename S> __device__ __forceinline__ void cfma(T &acc, const T a, const T b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+}
+
+// ----------------------------------------------------------------------------- batched GEMM
+// 64x64 output tile per CTA, 256 threads, 4x4 complex outputs per thread (rows ty+16i,
+// columns tx+16j), K staged through shared memory 16 at a time. Loads pick the
+// coalesced mapping from whichever operand stride is 1. Out-of-range rows/columns
+// of a tile are zero-filled on load and masked on store.
+template <typename R>
+__global__ void __launch_bounds__(256) zgemm_kernel(GemmDesc d, const typename cvec<R>::T *__restrict__ A,
+                                                    const typename cvec<R>::T *__restrict__ B,
+                                                    typename cvec<R>::T *__restrict__ C) {
+    typedef typename cvec<R>::T T;
+    constexpr int BM = 64, BN = 64, BK = 16;
+    __shared__ T As[BK][BM];
+    __shared__ T Bs[BK][BN];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const T alpha = {(R)d.alpha.x, (R)d.alpha.y};
+    const T beta = {(R)d.beta.x, (R)d.beta.y};
+    const bool use_beta = (d.beta.x != 0.0 || d.beta.y != 0.0);
+    for (int b = blockIdx.z; b < d.batch; b += gridDim.z) {
+        T acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = cz<T>();
+        for (int r = 0; r < d.nred; ++r) {
+            const T *Ab = A + d.offA[(i64)b * d.nred + r];
+            const T *Bb = B + d.offB[(i64)b * d.nred + r];
+            for (int k0 = 0; k0 < d.K; k0 += BK) {
+#pragma unroll
+                for (int s = 0; s < 4; ++s) {
+                    int l = tid + 256 * s, i, kk;
+                    if (d.csA == 1) { kk = l & 15; i = l >> 4; } else { i = l & 63; kk = l >> 6; }
+                    int m = m0 + i, k = k0 + kk;
+                    As[kk][i] = (m < d.M && k < d.K) ? Ab[(i64)m * d.rsA + (i64)k * d.csA] : cz<T>();
+                }
+#pragma unroll
+                for (int s = 0; s < 4; ++s) {
+                    int l = tid + 256 * s, nn, kk;
+                    if (d.csB == 1) { nn = l & 63; kk = l >> 6; } else { kk = l & 15; nn = l >> 4; }
+                    int n = n0 + nn, k = k0 + kk;
+                    Bs[kk][nn] = (n < d.N && k < d.K) ? Bb[(i64)k * d.rsB + (i64)n * d.csB] : cz<T>();
+                }
+                __syncthreads();
+#pragma unroll
+                for (int kk = 0; kk < BK; ++kk) {
+                    T a[4], bb[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) cfma<T, R>(acc[i][j], a[i], bb[j]);
+                }
+                __syncthreads();
+            }
+        }
+        T *Cb = C + d.offC[b];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            int m = m0 + ty + 16 * i;
+            if (m >= d.M) continue;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                int n = n0 + tx + 16 * j;
+                if (n >= d.N) continue;
+                T *c = Cb + (i64)m * d.rsC + (i64)n * d.csC;
+                T v;
+                v.x = alpha.x * acc[i][j].x - alpha.y * acc[i][j].y;
+                v.y = alpha.x * acc[i][j].y + alpha.y * acc[i][j].x;
+                if (use_beta) {
+                    T o = *c;
+                    v.x += beta.x * o.x - beta.y * o.y;
+                    v.y += beta.x * o.y + beta.y * o.x;
+                }
+                *c = v;
+            }
+        }
+    }
+}
+
+template <typename R>
+void launch_zgemm(const GemmDesc &d, const typename cvec<R>::T *A, const typename cvec<R>::T *B,
+                  typename cvec<R>::T *C, cudaStream_t st) {
+    if (d.batch <= 0 || d.M <= 0 || d.N <= 0) return;
+    dim3 grid((unsigned)ceil_div(d.N, 64), (unsigned)ceil_div(d.M, 64), (unsigned)(d.batch < 65535 ? d.batch : 65535));
+    zgemm_kernel<R><<<grid, 256, 0, st>>>(d, A, B, C);
+}
+template void launch_zgemm<double>(const GemmDesc &, const double2 *, const double2 *, double2 *, cudaStream_t);
+template void launch_zgemm<float>(const GemmDesc &, const float2 *, const float2 *, float2 *, cudaStream_t);
+
+// ----------------------------------------------------------------------------- batched permute-add
+template <typename R>
+__global__ void zpermute_kernel(PermDesc d, const typename cvec<R>::T *__restrict__ A, typename cvec<R>::T *C) {
+    typedef typename cvec<R>::T T;
+    const bool use_beta = (d.beta.x != 0.0 || d.beta.y != 0.0);
+    for (int b = blockIdx.y; b < d.batch; b += gridDim.y) {
+        const i64 oa0 = d.offA[b], oc0 = d.offC[b];
+        for (i64 idx = (i64)blockIdx.x * blockDim.x + threadIdx.x; idx < d.total; idx += (i64)gridDim.x * blockDim.x) {
+            i64 rem = idx, oa = oa0, oc = oc0;
+            for (int dd = d.nd - 1; dd >= 0; --dd) {
+                i64 q = rem / d.dims[dd];
+                i64 id = rem - q * d.dims[dd];
+                rem = q;
+                oa += id * d.sA[dd];
+                oc += id * d.sC[dd];
+            }
+            T a = A[oa];
+            T v;
+            v.x = (R)d.alpha.x * a.x - (R)d.alpha.y * a.y;
+            v.y = (R)d.alpha.x * a.y + (R)d.alpha.y * a.x;
+            if (use_beta) {
+                T c = C[oc];
+                v.x += (R)d.beta.x * c.x - (R)d.beta.y * c.y;
+                v.y += (R)d.beta.x * c.y + (R)d.beta.y * c.x;
+            }
+            C[oc] = v;
+        }
+    }
+}
+
+template <typename R>
+void launch_zpermute(const PermDesc &d, const typename cvec<R>::T *A, typename cvec<R>::T *C, cudaStream_t st) {
+    if (d.batch <= 0 || d.total <= 0) return;
+    i64 gx = ceil_div(d.total, 256);
+    if (gx > 4096) gx = 4096;
+    dim3 grid((unsigned)gx, (unsigned)(d.batch < 65535 ? d.batch : 65535));
+    zpermute_kernel<R><<<grid, 256, 0, st>>>(d, A, C);
+}
+template void launch_zpermute<double>(const PermDesc &, const double2 *, double2 *, cudaStream_t);
+template void launch_zpermute<float>(const PermDesc &, const float2 *, float2 *, cudaStream_t);
+
+// ----------------------------------------------------------------------------- ABI <-> internal layout
+// x: [nvec][D] (ABI), xt: [D][nv] (internal, columns >= nvec zero-filled)
+__global__ void transpose_in_kernel(const double2 *__restrict__ x, double2 *__restrict__ xt, i64 D, int nvec, int nv) {
+    __shared__ double2 tile[32][33];
+    i64 d0 = (i64)blockIdx.x * 32;
+    int v0 = blockIdx.y * 32;
+    int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+    for (int r = ty; r < 32; r += 8) {
+        int vv = v0 + r;
+        i64 dd = d0 + tx;
+        tile[r][tx] = (vv < nvec && dd < D) ? x[(i64)vv * D + dd] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        i64 dd = d0 + r;
+        int vv = v0 + tx;
+        if (dd < D && vv < nv) xt[dd * nv + vv] = tile[tx][r];
+    }
+}
+__global__ void transpose_out_kernel(const double2 *__restrict__ yt, double2 *__restrict__ y, i64 D, int nvec, int nv) {
+    __shared__ double2 tile[32][33];
+    i64 d0 = (i64)blockIdx.x * 32;
+    int v0 = blockIdx.y * 32;
+    int tx = threadIdx.x, ty = threadIdx.y;
+    for (int r = ty; r < 32; r += 8) {
+        i64 dd = d0 + r;
+        int vv = v0 + tx;
+        tile[r][tx] = (dd < D && vv < nv) ? yt[dd * nv + vv] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        int vv = v0 + r;
+        i64 dd = d0 + tx;
+        if (vv < nvec && dd < D) y[(i64)vv * D + dd] = tile[tx][r];
+    }
+}
+void launch_transpose_in(const double2 *x, double2 *xt, i64 D, int nvec, int nv, cudaStream_t st) {
+    dim3 grid((unsigned)ceil_div(D, 32), (unsigned)ceil_div(nv, 32));
+    transpose_in_kernel<<<grid, dim3(32, 8), 0, st>>>(x, xt, D, nvec, nv);
+}
+void launch_transpose_out(const double2 *yt, double2 *y, i64 D, int nvec, int nv, cudaStream_t st) {
+    dim3 grid((unsigned)ceil_div(D, 32), (unsigned)ceil_div(nv, 32));
+    transpose_out_kernel<<<grid, dim3(32, 8), 0, st>>>(yt, y, D, nvec, nv);
+}

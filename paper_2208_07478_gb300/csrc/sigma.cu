@@ -1,0 +1,644 @@
+// EOM-IP / EA-CCSD sigma vectors (Eq. 8 spaces, H_bar of Eq. 5) as plans of
+// batched complex GEMMs and permutes over momentum-conserving k-blocks.
+//
+// Vectors inside the library are element-major: row mu of the EOM space, nv
+// right-hand sides contiguous per row ([D][nv]). Every term of the spin-adapted
+// sigma then is a batched GEMM whose N dimension is (orbital index x nv):
+//
+//   EA (total momentum K), r2[kj,ka][j,a,b], kb = K + kj - ka
+//     s1[a]  = Fvv r1 + sum_{m,e} f_me (2 r2[km,K][m,a,e] - r2[km,km][m,e,a])
+//              + sum (2<am|ef> - <am|fe>) r2[km,ke][m,e,f]
+//     s2     = Wvvvo r1 + Fvv(a) r2 + Fvv(b) r2 - Foo(j) r2
+//              + sum_km [(2 Wovvo - Wovov) R' - Wovvo Q'] - sum_km Wovov r2   (ring terms)
+//              + sum_ke Wvvvv r2[kj,ke] - t2 . (sum (2<mn|ef> - <mn|fe>) r2)   (ladder, 3-body)
+//   IP (total momentum K), r2[ki,kj][i,j,a], ka = ki + kj - K: the mirror terms
+//     (Foo, Fov, 2<mn|ie> - <mn|ei>, Wovoo, Fvv, Foo(i), Foo(j), Woooo, ring, 3-body).
+//
+// Plans hold device offset tables (per batch entry and per momentum reduction),
+// built once per (sector, K, nv) and replayed on every call; the same plan runs
+// on the FP64 intermediates or on their FP32 copies.
+#include "ccgf_internal.h"
+
+namespace {
+
+struct PlanBuilder {
+    SigmaPlan *P;
+    std::vector<i64> off;   // host copy of the offset table
+
+    i64 push(const std::vector<i64> &v) {
+        i64 pos = (i64)off.size();
+        off.insert(off.end(), v.begin(), v.end());
+        return pos;
+    }
+    void gemm(int M, int N, int K, int nred, int a_buf, i64 rsA, i64 csA, const std::vector<i64> &oA, i64 rsB, i64 csB,
+              const std::vector<i64> &oB, int c_buf, i64 rsC, i64 csC, const std::vector<i64> &oC, double alpha, double beta) {
+        SigmaStep s{};
+        s.kind = STEP_GEMM;
+        s.g.M = M;
+        s.g.N = N;
+        s.g.K = K;
+        s.g.nred = nred;
+        s.g.batch = (int)oC.size();
+        s.g.rsA = rsA;
+        s.g.csA = csA;
+        s.g.rsB = rsB;
+        s.g.csB = csB;
+        s.g.rsC = rsC;
+        s.g.csC = csC;
+        s.g.alpha = make_double2(alpha, 0.0);
+        s.g.beta = make_double2(beta, 0.0);
+        s.a_buf = a_buf;
+        s.c_buf = c_buf;
+        s.offA_pos = push(oA);
+        s.offB_pos = push(oB);
+        s.offC_pos = push(oC);
+        P->steps.push_back(s);
+    }
+    // dims (outer..inner), source strides (scratch), destination strides
+    void perm(std::vector<i64> dims, std::vector<i64> sA, const std::vector<i64> &oA, int c_buf, std::vector<i64> sC,
+              const std::vector<i64> &oC, double alpha, double beta) {
+        SigmaStep s{};
+        s.kind = STEP_PERM;
+        s.p.nd = (int)dims.size();
+        s.p.total = 1;
+        for (int d = 0; d < s.p.nd; ++d) {
+            s.p.dims[d] = dims[d];
+            s.p.sA[d] = sA[d];
+            s.p.sC[d] = sC[d];
+            s.p.total *= dims[d];
+        }
+        s.p.batch = (int)oC.size();
+        s.p.alpha = make_double2(alpha, 0.0);
+        s.p.beta = make_double2(beta, 0.0);
+        s.a_buf = BUF_SCRATCH;
+        s.c_buf = c_buf;
+        s.offA_pos = push(oA);
+        s.offC_pos = push(oC);
+        P->steps.push_back(s);
+    }
+    void fov(int kind) {
+        SigmaStep s{};
+        s.kind = kind;
+        P->steps.push_back(s);
+    }
+};
+
+enum { SEG_X = 0, SEG_R, SEG_Q, SEG_T1, SEG_T3, SEG_XT, SEG_SMALL, SEG_END };
+
+void scratch_layout(const ccgf_handle *h, int nv, i64 seg[8]) {
+    const i64 nk2 = (i64)h->nk * h->nk, o = h->o, v = h->v;
+    i64 dmax = h->dim_ip > h->dim_ea ? h->dim_ip : h->dim_ea;
+    i64 r2max = nk2 * o * v * (o > v ? o : v);
+    i64 sizes[SEG_END] = {dmax * nv, r2max * nv, r2max * nv, r2max * nv, r2max * nv, r2max * nv, (o + v) * (i64)nv};
+    i64 pos = 0;
+    for (int s = 0; s < SEG_END; ++s) {
+        seg[s] = pos;
+        pos += (sizes[s] + 31) / 32 * 32;
+    }
+    seg[SEG_END] = pos;
+}
+
+SigmaPlan *build_plan_ea(const ccgf_handle *h, int K, int nv) {
+    const auto &km = h->km;
+    const int nk = h->nk, o = h->o, v = h->v;
+    SigmaPlan *P = new SigmaPlan();
+    P->sector = CCGF_SECTOR_EA;
+    P->K = K;
+    P->nv = nv;
+    scratch_layout(h, nv, P->seg);
+    P->scratch_elems = P->seg[SEG_END];
+    PlanBuilder B{P, {}};
+    const i64 S2 = (i64)o * v * v, NV = nv;
+    const i64 sx = P->seg[SEG_X];
+    auto row = [&](int kj, int ka) -> i64 { return v + ((i64)kj * nk + ka) * S2; };
+    const i64 v2 = (i64)v * v, ov = (i64)o * v, nk2 = (i64)nk * nk;
+
+    // s1[a] = Fvv[K] r1 (first write)
+    B.gemm(v, nv, v, 1, BUF_FVV, v, 1, {(i64)K * v2}, NV, 1, {sx}, BUF_Y, NV, 1, {0}, 1.0, 0.0);
+    B.fov(STEP_FOV_EA);
+    // s1 += sum (2<am|ef> - <am|fe>) r2
+    B.gemm(v, nv, (int)(nk2 * o * v2), 1, BUF_UVOVV, nk2 * o * v2, 1, {(i64)K * v * nk2 * o * v2}, NV, 1, {sx + v * NV},
+           BUF_Y, NV, 1, {0}, 1.0, 1.0);
+    // s2 = Wvvvo r1 (first write of every block)
+    {
+        std::vector<i64> oA, oB, oC;
+        for (int kj = 0; kj < nk; ++kj)
+            for (int ka = 0; ka < nk; ++ka) {
+                int kb = km.c(K, ka, kj);
+                oA.push_back((((i64)ka * nk + kb) * nk + K) * (o * v2 * v));
+                oB.push_back(sx);
+                oC.push_back(row(kj, ka) * NV);
+            }
+        B.gemm((int)(o * v2), nv, v, 1, BUF_WVVVO, v, 1, oA, NV, 1, oB, BUF_Y, NV, 1, oC, 1.0, 0.0);
+    }
+    // s2 += Fvv[ka](a,e) r2[j,e,b]
+    {
+        std::vector<i64> oA, oB, oC;
+        for (int kj = 0; kj < nk; ++kj)
+            for (int ka = 0; ka < nk; ++ka)
+                for (int j = 0; j < o; ++j) {
+                    oA.push_back((i64)ka * v2);
+                    oB.push_back(sx + (row(kj, ka) + j * v2) * NV);
+                    oC.push_back((row(kj, ka) + j * v2) * NV);
+                }
+        B.gemm(v, (int)(v * NV), v, 1, BUF_FVV, v, 1, oA, v * NV, 1, oB, BUF_Y, v * NV, 1, oC, 1.0, 1.0);
+    }
+    // s2 += Fvv[kb](b,e) r2[j,a,e]
+    {
+        std::vector<i64> oA, oB, oC;
+        for (int kj = 0; kj < nk; ++kj)
+            for (int ka = 0; ka < nk; ++ka) {
+                int kb = km.c(K, ka, kj);
+                for (int j = 0; j < o; ++j)
+                    for (int a = 0; a < v; ++a) {
+                        i64 r = row(kj, ka) + (j * v + a) * (i64)v;
+                        oA.push_back((i64)kb * v2);
+                        oB.push_back(sx + r * NV);
+                        oC.push_back(r * NV);
+                    }
+            }
+        B.gemm(v, nv, v, 1, BUF_FVV, v, 1, oA, NV, 1, oB, BUF_Y, NV, 1, oC, 1.0, 1.0);
+    }
+    // s2 -= Foo[kj](m,j) r2[m,a,b]
+    {
+        std::vector<i64> oA, oB, oC;
+        for (int kj = 0; kj < nk; ++kj)
+            for (int ka = 0; ka < nk; ++ka) {
+                oA.push_back((i64)kj * o * o);
+                oB.push_back(sx + row(kj, ka) * NV);
+                oC.push_back(row(kj, ka) * NV);
+            }
+        B.gemm(o, (int)(v2 * NV), o, 1, BUF_FOO, 1, o, oA, v2 * NV, 1, oB, BUF_Y, v2 * NV, 1, oC, -1.0, 1.0);
+    }
+    // R'[ka][km][m][e][a] = r2[km,ka][m,a,e]
+    {
+        std::vector<i64> oA, oC;
+        for (int ka = 0; ka < nk; ++ka)
+            for (int kmm = 0; kmm < nk; ++kmm) {
+                oA.push_back(sx + row(kmm, ka) * NV);
+                oC.push_back(P->seg[SEG_R] + ((i64)ka * nk + kmm) * S2 * NV);
+            }
+        B.perm({o, v, v, NV}, {v2 * NV, NV, v * NV, 1}, oA, BUF_SCRATCH, {v2 * NV, v * NV, NV, 1}, oC, 1.0, 0.0);
+    }
+    // ring: T1[kj][ka][j][b][a] = sum_km W1[kb][kj][km] R'[ka][km] + W2[kb][kj][km] Q'[ka][km], Q' = r2[km,ke][m,e,a]
+    {
+        std::vector<i64> oA, oB, oC;
+        const i64 blk = ov * ov;
+        for (int kj = 0; kj < nk; ++kj)
+            for (int ka = 0; ka < nk; ++ka) {
+                int kb = km.c(K, ka, kj);
+                for (int kmm = 0; kmm < nk; ++kmm) {
+                    int ke = km.c(K, ka, kmm);
+                    oA.push_back(0 * h->wov_seg + (((i64)kb * nk + kj) * nk + kmm) * blk);
+                    oB.push_back(P->seg[SEG_R] + ((i64)ka * nk + kmm) * S2 * NV);
+                    oA.push_back(1 * h->wov_seg + (((i64)kb * nk + kj) * nk + kmm) * blk);
+                    oB.push_back(sx + row(kmm, ke) * NV);
+                }
+                oC.push_back(P->seg[SEG_T1] + ((i64)kj * nk + ka) * S2 * NV);
+            }
+        B.gemm((int)ov, (int)(v * NV), (int)ov, 2 * nk, BUF_WOV3, ov, 1, oA, v * NV, 1, oB, BUF_SCRATCH, v * NV, 1, oC, 1.0,
+               0.0);
+        std::vector<i64> pA, pC;
+        for (int kj = 0; kj < nk; ++kj)
+            for (int ka = 0; ka < nk; ++ka) {
+                pA.push_back(P->seg[SEG_T1] + ((i64)kj * nk + ka) * S2 * NV);
+                pC.push_back(row(kj, ka) * NV);
+            }
+        B.perm({o, v, v, NV}, {v2 * NV, v * NV, NV, 1}, pA, BUF_Y, {v2 * NV, NV, v * NV, 1}, pC, 1.0, 1.0);
+    }
+    // ring: s2[j,a,b] += sum_km WN[ka][kj][km](j,a;m,e) r2[km,ke2][m,e,b], ke2 = km + ka - kj
+    {
+        std::vector<i64> oA, oB, oC;
+        const i64 blk = ov * ov;
+        for (int kj = 0; kj < nk; ++kj)
+            for (int ka = 0; ka < nk; ++ka) {
+                for (int kmm = 0; kmm < nk; ++kmm) {
+                    int ke2 = km.c(kmm, kj, ka);
+                    oA.push_back(2 * h->wov_seg + (((i64)ka * nk + kj) * nk + kmm) * blk);
+                    oB.push_back(sx + row(kmm, ke2) * NV);
+                }
+                oC.push_back(row(kj, ka) * NV);
+            }
+        B.gemm((int)ov, (int)(v * NV), (int)ov, nk, BUF_WOV3, ov, 1, oA, v * NV, 1, oB, BUF_Y, v * NV, 1, oC, 1.0, 1.0);
+    }
+    // ladder: XT[kj][ke][e][f][j] = r2[kj,ke][j,e,f];  T3[kj][ka][a][b][j] = Wvvvv[ka,kb] XT[kj];  s2 += T3
+    {
+        std::vector<i64> oA, oC;
+        for (int kj = 0; kj < nk; ++kj)
+            for (int ke = 0; ke < nk; ++ke) {
+                oA.push_back(sx + row(kj, ke) * NV);
+                oC.push_back(P->seg[SEG_XT] + ((i64)kj * nk + ke) * S2 * NV);
+            }
+        B.perm({v, v, o, NV}, {v * NV, NV, v2 * NV, 1}, oA, BUF_SCRATCH, {o * v * NV, o * NV, NV, 1}, oC, 1.0, 0.0);
+        std::vector<i64> gA, gB, gC;
+        for (int kj = 0; kj < nk; ++kj)
+            for (int ka = 0; ka < nk; ++ka) {
+                int kb = km.c(K, ka, kj);
+                gA.push_back(((i64)ka * nk + kb) * v2 * nk * v2);
+                gB.push_back(P->seg[SEG_XT] + (i64)kj * nk * S2 * NV);
+                gC.push_back(P->seg[SEG_T3] + ((i64)kj * nk + ka) * S2 * NV);
+            }
+        B.gemm((int)v2, (int)(o * NV), (int)(nk * v2), 1, BUF_WVVVV, nk * v2, 1, gA, o * NV, 1, gB, BUF_SCRATCH, o * NV, 1, gC,
+               1.0, 0.0);
+        std::vector<i64> pA, pC;
+        for (int kj = 0; kj < nk; ++kj)
+            for (int ka = 0; ka < nk; ++ka) {
+                pA.push_back(P->seg[SEG_T3] + ((i64)kj * nk + ka) * S2 * NV);
+                pC.push_back(row(kj, ka) * NV);
+            }
+        B.perm({v, v, o, NV}, {v * o * NV, o * NV, NV, 1}, pA, BUF_Y, {v * NV, NV, v2 * NV, 1}, pC, 1.0, 1.0);
+    }
+    // three-body: Ysm[m] = sum (2<mn|ef> - <mn|fe>) r2[kn,ke][n,e,f];  s2 -= t2[K,kj,ka][m,j,a,b] Ysm[m]
+    {
+        const i64 sm = P->seg[SEG_SMALL];
+        B.gemm(o, nv, (int)(nk2 * o * v2), 1, BUF_UOOVV_EA, nk2 * o * v2, 1, {(i64)K * o * nk2 * o * v2}, NV, 1,
+               {sx + v * NV}, BUF_SCRATCH, NV, 1, {sm}, 1.0, 0.0);
+        std::vector<i64> oA, oB, oC;
+        for (int kj = 0; kj < nk; ++kj)
+            for (int ka = 0; ka < nk; ++ka) {
+                oA.push_back((((i64)K * nk + kj) * nk + ka) * S2 * o);
+                oB.push_back(sm);
+                oC.push_back(row(kj, ka) * NV);
+            }
+        B.gemm((int)S2, nv, o, 1, BUF_T2EA, o, 1, oA, NV, 1, oB, BUF_Y, NV, 1, oC, -1.0, 1.0);
+    }
+    P->host_off = B.off;
+    return P;
+}
+
+SigmaPlan *build_plan_ip(const ccgf_handle *h, int K, int nv) {
+    const auto &km = h->km;
+    const int nk = h->nk, o = h->o, v = h->v;
+    SigmaPlan *P = new SigmaPlan();
+    P->sector = CCGF_SECTOR_IP;
+    P->K = K;
+    P->nv = nv;
+    scratch_layout(h, nv, P->seg);
+    P->scratch_elems = P->seg[SEG_END];
+    PlanBuilder B{P, {}};
+    const i64 S2 = (i64)o * o * v, NV = nv;
+    const i64 sx = P->seg[SEG_X];
+    auto row = [&](int ki, int kj) -> i64 { return o + ((i64)ki * nk + kj) * S2; };
+    const i64 o2 = (i64)o * o, ov = (i64)o * v, nk2 = (i64)nk * nk;
+
+    // s1 = -Foo[K]^T r1
+    B.gemm(o, nv, o, 1, BUF_FOO, 1, o, {(i64)K * o2}, NV, 1, {sx}, BUF_Y, NV, 1, {0}, -1.0, 0.0);
+    B.fov(STEP_FOV_IP);
+    // s1 -= sum (2<mn|ie> - <mn|ei>) r2
+    B.gemm(o, nv, (int)(nk2 * S2), 1, BUF_UOOOV, nk2 * S2, 1, {(i64)K * o * nk2 * S2}, NV, 1, {sx + o * NV}, BUF_Y, NV, 1,
+           {0}, -1.0, 1.0);
+    // s2 = -Wovoo r1 (first write)
+    {
+        std::vector<i64> oA, oB, oC;
+        for (int ki = 0; ki < nk; ++ki)
+            for (int kj = 0; kj < nk; ++kj) {
+                oA.push_back((((i64)K * nk + ki) * nk + kj) * S2 * o);
+                oB.push_back(sx);
+                oC.push_back(row(ki, kj) * NV);
+            }
+        B.gemm((int)S2, nv, o, 1, BUF_WOVOO, o, 1, oA, NV, 1, oB, BUF_Y, NV, 1, oC, -1.0, 0.0);
+    }
+    // s2 += Fvv[ka](a,e) r2[i,j,e]
+    {
+        std::vector<i64> oA, oB, oC;
+        for (int ki = 0; ki < nk; ++ki)
+            for (int kj = 0; kj < nk; ++kj) {
+                int ka = km.c(ki, K, kj);
+                for (int ij = 0; ij < o * o; ++ij) {
+                    i64 r = row(ki, kj) + (i64)ij * v;
+                    oA.push_back((i64)ka * v * v);
+                    oB.push_back(sx + r * NV);
+                    oC.push_back(r * NV);
+                }
+            }
+        B.gemm(v, nv, v, 1, BUF_FVV, v, 1, oA, NV, 1, oB, BUF_Y, NV, 1, oC, 1.0, 1.0);
+    }
+    // s2 -= Foo[ki](m,i) r2[m,j,a]
+    {
+        std::vector<i64> oA, oB, oC;
+        for (int ki = 0; ki < nk; ++ki)
+            for (int kj = 0; kj < nk; ++kj) {
+                oA.push_back((i64)ki * o2);
+                oB.push_back(sx + row(ki, kj) * NV);
+                oC.push_back(row(ki, kj) * NV);
+            }
+        B.gemm(o, (int)(ov * NV), o, 1, BUF_FOO, 1, o, oA, ov * NV, 1, oB, BUF_Y, ov * NV, 1, oC, -1.0, 1.0);
+    }
+    // s2 -= Foo[kj](m,j) r2[i,m,a]
+    {
+        std::vector<i64> oA, oB, oC;
+        for (int ki = 0; ki < nk; ++ki)
+            for (int kj = 0; kj < nk; ++kj)
+                for (int i = 0; i < o; ++i) {
+                    oA.push_back((i64)kj * o2);
+                    oB.push_back(sx + (row(ki, kj) + i * ov) * NV);
+                    oC.push_back((row(ki, kj) + i * ov) * NV);
+                }
+        B.gemm(o, (int)(v * NV), o, 1, BUF_FOO, 1, o, oA, v * NV, 1, oB, BUF_Y, v * NV, 1, oC, -1.0, 1.0);
+    }
+    // s2 += sum_km Woooo[ki][kj](i,j;km,m,n) r2[km,kn][m,n,a]
+    {
+        std::vector<i64> oA, oB, oC;
+        for (int ki = 0; ki < nk; ++ki)
+            for (int kj = 0; kj < nk; ++kj) {
+                for (int kmm = 0; kmm < nk; ++kmm) {
+                    int kn = km.c(ki, kmm, kj);
+                    oA.push_back(((i64)ki * nk + kj) * o2 * nk * o2 + (i64)kmm * o2);
+                    oB.push_back(sx + row(kmm, kn) * NV);
+                }
+                oC.push_back(row(ki, kj) * NV);
+            }
+        B.gemm((int)o2, (int)(v * NV), (int)o2, nk, BUF_WOOOO, nk * o2, 1, oA, v * NV, 1, oB, BUF_Y, v * NV, 1, oC, 1.0, 1.0);
+    }
+    // R'[ki][km][m][e][i] = r2[ki,km][i,m,e];  Q'[kj][km][m][e][j] = r2[km,kj][m,j,e]
+    {
+        std::vector<i64> oA, oC;
+        for (int ki = 0; ki < nk; ++ki)
+            for (int kmm = 0; kmm < nk; ++kmm) {
+                oA.push_back(sx + row(ki, kmm) * NV);
+                oC.push_back(P->seg[SEG_R] + ((i64)ki * nk + kmm) * S2 * NV);
+            }
+        B.perm({o, v, o, NV}, {v * NV, NV, ov * NV, 1}, oA, BUF_SCRATCH, {v * o * NV, o * NV, NV, 1}, oC, 1.0, 0.0);
+        std::vector<i64> qA, qC;
+        for (int kj = 0; kj < nk; ++kj)
+            for (int kmm = 0; kmm < nk; ++kmm) {
+                qA.push_back(sx + row(kmm, kj) * NV);
+                qC.push_back(P->seg[SEG_Q] + ((i64)kj * nk + kmm) * S2 * NV);
+            }
+        B.perm({o, v, o, NV}, {ov * NV, NV, v * NV, 1}, qA, BUF_SCRATCH, {v * o * NV, o * NV, NV, 1}, qC, 1.0, 0.0);
+    }
+    const i64 blk = ov * ov;
+    // ring: T1[ki][kj][j][a][i] = sum_km W1[ka][kj][km] R'[ki][km] + W2[ka][kj][km] Q'[ki][km]
+    {
+        std::vector<i64> oA, oB, oC;
+        for (int ki = 0; ki < nk; ++ki)
+            for (int kj = 0; kj < nk; ++kj) {
+                int ka = km.c(ki, K, kj);
+                for (int kmm = 0; kmm < nk; ++kmm) {
+                    oA.push_back(0 * h->wov_seg + (((i64)ka * nk + kj) * nk + kmm) * blk);
+                    oB.push_back(P->seg[SEG_R] + ((i64)ki * nk + kmm) * S2 * NV);
+                    oA.push_back(1 * h->wov_seg + (((i64)ka * nk + kj) * nk + kmm) * blk);
+                    oB.push_back(P->seg[SEG_Q] + ((i64)ki * nk + kmm) * S2 * NV);
+                }
+                oC.push_back(P->seg[SEG_T1] + ((i64)ki * nk + kj) * S2 * NV);
+            }
+        B.gemm((int)ov, (int)(o * NV), (int)ov, 2 * nk, BUF_WOV3, ov, 1, oA, o * NV, 1, oB, BUF_SCRATCH, o * NV, 1, oC, 1.0,
+               0.0);
+        std::vector<i64> pA, pC;
+        for (int ki = 0; ki < nk; ++ki)
+            for (int kj = 0; kj < nk; ++kj) {
+                pA.push_back(P->seg[SEG_T1] + ((i64)ki * nk + kj) * S2 * NV);
+                pC.push_back(row(ki, kj) * NV);
+            }
+        // T1 [j][a][i] -> s2 [i][j][a]
+        B.perm({o, v, o, NV}, {v * o * NV, o * NV, NV, 1}, pA, BUF_Y, {v * NV, NV, ov * NV, 1}, pC, 1.0, 1.0);
+    }
+    // ring: T3[ki][kj][i][a][j] = sum_km WN[ka][ki][km] Q'[kj][km]
+    {
+        std::vector<i64> oA, oB, oC;
+        for (int ki = 0; ki < nk; ++ki)
+            for (int kj = 0; kj < nk; ++kj) {
+                int ka = km.c(ki, K, kj);
+                for (int kmm = 0; kmm < nk; ++kmm) {
+                    oA.push_back(2 * h->wov_seg + (((i64)ka * nk + ki) * nk + kmm) * blk);
+                    oB.push_back(P->seg[SEG_Q] + ((i64)kj * nk + kmm) * S2 * NV);
+                }
+                oC.push_back(P->seg[SEG_T3] + ((i64)ki * nk + kj) * S2 * NV);
+            }
+        B.gemm((int)ov, (int)(o * NV), (int)ov, nk, BUF_WOV3, ov, 1, oA, o * NV, 1, oB, BUF_SCRATCH, o * NV, 1, oC, 1.0, 0.0);
+        std::vector<i64> pA, pC;
+        for (int ki = 0; ki < nk; ++ki)
+            for (int kj = 0; kj < nk; ++kj) {
+                pA.push_back(P->seg[SEG_T3] + ((i64)ki * nk + kj) * S2 * NV);
+                pC.push_back(row(ki, kj) * NV);
+            }
+        // T3 [i][a][j] -> s2 [i][j][a]
+        B.perm({o, v, o, NV}, {v * o * NV, o * NV, NV, 1}, pA, BUF_Y, {ov * NV, NV, v * NV, 1}, pC, 1.0, 1.0);
+    }
+    // three-body: Xsm[e] = sum (2<mn|ef> - <mn|fe>) r2[km,kn][m,n,f];  s2 -= t2[ki,kj,K][i,j,e,a] Xsm[e]
+    {
+        const i64 sm = P->seg[SEG_SMALL];
+        B.gemm(v, nv, (int)(nk2 * S2), 1, BUF_UOOVV_IP, nk2 * S2, 1, {(i64)K * v * nk2 * S2}, NV, 1, {sx + o * NV},
+               BUF_SCRATCH, NV, 1, {sm}, 1.0, 0.0);
+        std::vector<i64> oA, oB, oC;
+        for (int ki = 0; ki < nk; ++ki)
+            for (int kj = 0; kj < nk; ++kj) {
+                oA.push_back((((i64)ki * nk + kj) * nk + K) * S2 * v);
+                oB.push_back(sm);
+                oC.push_back(row(ki, kj) * NV);
+            }
+        B.gemm((int)S2, nv, v, 1, BUF_T2IP, v, 1, oA, NV, 1, oB, BUF_Y, NV, 1, oC, -1.0, 1.0);
+    }
+    P->host_off = B.off;
+    return P;
+}
+
+// ---------------------------------------------------------------- Fov terms
+// IP: y1[i] += sum_{km,m,e} f_me (2 x2[K,km][i,m,e] - x2[km,K][m,i,e])
+// EA: y1[a] += sum_{km,m,e} f_me (2 x2[km,K][m,a,e] - x2[km,km][m,e,a])
+template <typename T, typename R>
+__global__ void fov_kernel(int sector, int K, int nk, int o, int v, int nv, const T *__restrict__ Fov,
+                           const T *__restrict__ x, T *__restrict__ y) {
+    const int nrow = sector == CCGF_SECTOR_IP ? o : v;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= nrow * nv) return;
+    const int p = tid / nv, c = tid % nv;
+    R ax = 0, ay = 0;
+    if (sector == CCGF_SECTOR_IP) {
+        const i64 S2 = (i64)o * o * v;
+        for (int kmm = 0; kmm < nk; ++kmm) {
+            const T *a = x + (o + ((i64)K * nk + kmm) * S2) * nv;
+            const T *b = x + (o + ((i64)kmm * nk + K) * S2) * nv;
+            for (int m = 0; m < o; ++m)
+                for (int e = 0; e < v; ++e) {
+                    T f = Fov[((i64)kmm * o + m) * v + e];
+                    T u = a[((i64)(p * o + m) * v + e) * nv + c];
+                    T w = b[((i64)(m * o + p) * v + e) * nv + c];
+                    R zx = 2 * u.x - w.x, zy = 2 * u.y - w.y;
+                    ax += f.x * zx - f.y * zy;
+                    ay += f.x * zy + f.y * zx;
+                }
+        }
+    } else {
+        const i64 S2 = (i64)o * v * v;
+        for (int kmm = 0; kmm < nk; ++kmm) {
+            const T *a = x + (v + ((i64)kmm * nk + K) * S2) * nv;
+            const T *b = x + (v + ((i64)kmm * nk + kmm) * S2) * nv;
+            for (int m = 0; m < o; ++m)
+                for (int e = 0; e < v; ++e) {
+                    T f = Fov[((i64)kmm * o + m) * v + e];
+                    T u = a[((i64)(m * v + p) * v + e) * nv + c];
+                    T w = b[((i64)(m * v + e) * v + p) * nv + c];
+                    R zx = 2 * u.x - w.x, zy = 2 * u.y - w.y;
+                    ax += f.x * zx - f.y * zy;
+                    ay += f.x * zy + f.y * zx;
+                }
+        }
+    }
+    T out = y[(i64)p * nv + c];
+    out.x += ax;
+    out.y += ay;
+    y[(i64)p * nv + c] = out;
+}
+
+template <typename R>
+__global__ void convert_kernel(const double2 *__restrict__ a, typename cvec<R>::T *__restrict__ b, i64 n) {
+    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
+        typename cvec<R>::T t;
+        t.x = (R)a[i].x;
+        t.y = (R)a[i].y;
+        b[i] = t;
+    }
+}
+__global__ void widen_kernel(const float2 *__restrict__ a, double2 *__restrict__ b, i64 n) {
+    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
+        b[i] = make_double2((double)a[i].x, (double)a[i].y);
+}
+inline unsigned gsz(i64 n) {
+    i64 g = ceil_div(n, 256);
+    return (unsigned)(g > 152 * 32 ? 152 * 32 : (g > 0 ? g : 1));
+}
+
+template <typename R>
+void run_plan(ccgf_handle *h, SigmaPlan *P, const double2 *x, double2 *y, cudaStream_t st) {
+    typedef typename cvec<R>::T T;
+    const bool f64 = sizeof(R) == 8;
+    T *scr = f64 ? (T *)h->scratch.p : (T *)h->scratch_f.p;
+    const i64 D = P->sector == CCGF_SECTOR_IP ? h->dim_ip : h->dim_ea;
+    const i64 n = D * P->nv;
+    T *yout = f64 ? (T *)y : (T *)h->yf.p;
+    // input -> scratch segment X (copy or narrowing conversion)
+    convert_kernel<R><<<gsz(n), 256, 0, st>>>(x, scr + P->seg[SEG_X], n);
+    h->launches++;
+    const i64 *offs = P->offsets.p;
+    for (const SigmaStep &s : P->steps) {
+        T *C = s.c_buf == BUF_Y ? yout : scr;
+        if (s.kind == STEP_GEMM) {
+            GemmDesc d = s.g;
+            d.offA = offs + s.offA_pos;
+            d.offB = offs + s.offB_pos;
+            d.offC = offs + s.offC_pos;
+            const T *A = f64 ? (const T *)h->W[s.a_buf].p : (const T *)h->Wf[s.a_buf].p;
+            launch_zgemm<R>(d, A, scr, C, st);
+        } else if (s.kind == STEP_PERM) {
+            PermDesc d = s.p;
+            d.offA = offs + s.offA_pos;
+            d.offC = offs + s.offC_pos;
+            launch_zpermute<R>(d, scr, C, st);
+        } else {
+            const int sector = s.kind == STEP_FOV_IP ? CCGF_SECTOR_IP : CCGF_SECTOR_EA;
+            const int nrow = sector == CCGF_SECTOR_IP ? h->o : h->v;
+            const T *F = f64 ? (const T *)h->W[BUF_FOV].p : (const T *)h->Wf[BUF_FOV].p;
+            fov_kernel<T, R><<<(unsigned)ceil_div((i64)nrow * P->nv, 128), 128, 0, st>>>(
+                sector, P->K, h->nk, h->o, h->v, P->nv, F, scr + P->seg[SEG_X], yout);
+        }
+        h->launches++;
+    }
+    if (!f64) {
+        widen_kernel<<<gsz(n), 256, 0, st>>>(h->yf.p, y, n);
+        h->launches++;
+    }
+}
+
+// Host-side proof that every access of every launch of a plan stays inside its buffer:
+// for each batch entry the largest address is offset + sum (extent - 1) * |stride| (all strides
+// are non-negative here), compared with the buffer length in complex elements.
+bool check_plan(const ccgf_handle *h, const SigmaPlan *P, const std::vector<i64> &off, std::string &why) {
+    const i64 D = P->sector == CCGF_SECTOR_IP ? h->dim_ip : h->dim_ea;
+    const i64 ylen = D * P->nv, slen = P->scratch_elems;
+    int si = 0;
+    for (const SigmaStep &s : P->steps) {
+        ++si;
+        if (s.kind == STEP_GEMM) {
+            const GemmDesc &g = s.g;
+            const i64 alen = h->W[s.a_buf].n, clen = s.c_buf == BUF_Y ? ylen : slen;
+            const i64 spanA = (i64)(g.M - 1) * g.rsA + (i64)(g.K - 1) * g.csA;
+            const i64 spanB = (i64)(g.K - 1) * g.rsB + (i64)(g.N - 1) * g.csB;
+            const i64 spanC = (i64)(g.M - 1) * g.rsC + (i64)(g.N - 1) * g.csC;
+            for (int b = 0; b < g.batch; ++b) {
+                for (int r = 0; r < g.nred; ++r) {
+                    i64 oa = off[s.offA_pos + (i64)b * g.nred + r], ob = off[s.offB_pos + (i64)b * g.nred + r];
+                    if (oa < 0 || oa + spanA >= alen) { why = "gemm A out of range at step " + std::to_string(si); return false; }
+                    if (ob < 0 || ob + spanB >= slen) { why = "gemm B out of range at step " + std::to_string(si); return false; }
+                }
+                i64 oc = off[s.offC_pos + b];
+                if (oc < 0 || oc + spanC >= clen) { why = "gemm C out of range at step " + std::to_string(si); return false; }
+            }
+        } else if (s.kind == STEP_PERM) {
+            const PermDesc &p = s.p;
+            i64 spanA = 0, spanC = 0;
+            for (int d = 0; d < p.nd; ++d) {
+                spanA += (p.dims[d] - 1) * p.sA[d];
+                spanC += (p.dims[d] - 1) * p.sC[d];
+            }
+            const i64 clen = s.c_buf == BUF_Y ? ylen : slen;
+            for (int b = 0; b < p.batch; ++b) {
+                i64 oa = off[s.offA_pos + b], oc = off[s.offC_pos + b];
+                if (oa < 0 || oa + spanA >= slen) { why = "permute source out of range at step " + std::to_string(si); return false; }
+                if (oc < 0 || oc + spanC >= clen) { why = "permute destination out of range at step " + std::to_string(si); return false; }
+            }
+        }
+    }
+    return true;
+}
+
+}  // namespace
+
+void free_plans(ccgf_handle *h) {
+    for (SigmaPlan *p : h->plans)
+        if (p) {
+            dfree(p->offsets);
+            delete p;
+        }
+    h->plans.assign(h->plans.size(), nullptr);
+}
+
+ccgf_status sigma_apply(ccgf_handle *h, int sector, int K, int nv, const double2 *x, double2 *y, ccgf_precision prec,
+                        cudaStream_t st) {
+    if (nv != h->plan_nv) {
+        // plans and scratch are sized for nv columns; rebuild on change
+        CCGF_CUDA_TRY(cudaStreamSynchronize(st));
+        free_plans(h);
+        h->plan_nv = nv;
+    }
+    if (h->plans.empty()) h->plans.assign(2 * h->nk, nullptr);
+    SigmaPlan *&P = h->plans[(sector - 1) * h->nk + K];
+    if (!P) {
+        SigmaPlan *np = sector == CCGF_SECTOR_IP ? build_plan_ip(h, K, nv) : build_plan_ea(h, K, nv);
+        std::string why;
+        if (!check_plan(h, np, np->host_off, why)) {
+            delete np;
+            set_last_error("internal sigma plan failed its bound check: " + why);
+            return CCGF_ERR_INVALID_ARG;
+        }
+        ccgf_status s = dalloc(np->offsets, (i64)np->host_off.size());
+        if (s != CCGF_OK) { delete np; return s; }
+        CCGF_CUDA_TRY(cudaMemcpy(np->offsets.p, np->host_off.data(), sizeof(i64) * np->host_off.size(), cudaMemcpyHostToDevice));
+        P = np;
+    }
+    const i64 D = sector == CCGF_SECTOR_IP ? h->dim_ip : h->dim_ea;
+    if (prec == CCGF_FP64) {
+        if (h->scratch.n < P->scratch_elems) {
+            CCGF_CUDA_TRY(cudaStreamSynchronize(st));
+            dfree(h->scratch);
+            CCGF_TRY(dalloc(h->scratch, P->scratch_elems));
+        }
+        run_plan<double>(h, P, x, y, st);
+    } else {
+        if (h->scratch_f.n < P->scratch_elems || h->yf.n < D * nv) {
+            CCGF_CUDA_TRY(cudaStreamSynchronize(st));
+            if (h->scratch_f.n < P->scratch_elems) {
+                dfree(h->scratch_f);
+                CCGF_TRY(dalloc(h->scratch_f, P->scratch_elems));
+            }
+            i64 dmax = h->dim_ip > h->dim_ea ? h->dim_ip : h->dim_ea;
+            if (h->yf.n < dmax * nv) {
+                dfree(h->yf);
+                CCGF_TRY(dalloc(h->yf, dmax * nv));
+            }
+        }
+        run_plan<float>(h, P, x, y, st);
+    }
+    CCGF_CUDA_TRY(cudaGetLastError());
+    return CCGF_OK;
+}
