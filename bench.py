@@ -1,0 +1,397 @@
+"""Benchmark of the periodic CCGF hot path on GB300.
+
+Workload (default): the Si-like 2x2x2 k-mesh system, nocc = 4, nvir = 22 per k,
+Naux = 96, 64 frequencies in [-0.8, 0.8] Ha, eta = 0.005 Ha, both sectors,
+synthetic seeded inputs. One step = one frequency point: for all 8 k-points
+and all 26 orbitals, the removal (IP) and addition (EA) shifted systems are
+solved by batched GMRES to relative residual 1e-6 and contracted into
+G_pq(k, w) (8 * 26^2 = 5408 complex elements per step). Successive steps take
+successive points of the frequency grid. The timed region also holds one build
+of the similarity-transformed Hamiltonian blocks from device-resident inputs,
+amortised over the K steps.
+
+`value` is the plain FP64 form (every step in FP64). The chosen form (FP32
+sigma inside FP64 refinement, same FP64-verified residual target) is reported
+beside it with its ratio to the plain form.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+Under torchrun every rank solves its own frequency points (no data-path
+collective); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "G_pq(k,ω) elements/s at rel. residual 1e-6; sigma TFLOP/s vs GB300 peak"
+WORKLOAD = "si_k222_o4v22"
+TOL = 1e-6
+# FP64 SIMT peak: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (the nominal 1.25 TFLOP/s of the part)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-chosen", action="store_true", help="skip the chosen-form measurement")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- distributed
+def dist_setup(n):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("CCGF_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return rank, world, local, pg
+
+
+def barrier(pg, device=None):
+    if pg is not None:
+        if device is not None:
+            pg.barrier(device_ids=[device])
+        else:
+            pg.barrier()
+
+
+def max_over_ranks(pg, x, device):
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def gpu_arm(args):
+    import torch
+    from paper_2208_07478_gb300 import binding as B
+    from paper_2208_07478_gb300.synth import make_workload, WORKLOADS
+
+    rank, world, local, pg = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    cfg = WORKLOADS[args.workload]
+    s = make_workload(args.workload)
+    nk, N = s.nk, s.nmo
+    elems_per_step = nk * N * N
+    nomega = len(s.omega)
+
+    def to_dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    dL, dt1, dt2, deps = to_dev(s.L), to_dev(s.t1), to_dev(s.t2), to_dev(s.mo_energy)
+    Gd = torch.zeros((nk, 1, N, N), dtype=torch.complex128, device=dev)
+
+    def omega_for(step):
+        # rank-strided walk over the frequency grid: ranks never share a point
+        return s.omega[[(rank + world * step) % nomega]]
+
+    def build():
+        return B.build_intermediates(s.kmesh, s.nocc, s.nvir, s.naux, deps, dL, dt1, dt2, on_device=True, stream=stream)
+
+    def run_steps(h, prec, first, count):
+        stats = []
+        for k in range(count):
+            opt = B.default_options(prec=prec, tol=TOL, restart_m=40, max_iter=4000, max_refine=40)
+            status, st = B.solve_gf(h, B.BOTH, omega_for(first + k), s.eta, Gd, options=opt, on_device=True,
+                                    stream=stream)
+            if status != B.CCGF_OK:
+                raise RuntimeError(f"solve did not converge (status {status})")
+            stats.append(st)
+        return stats
+
+    def timed(prec, first):
+        """warm-up steps, then build + K steps between synchronised barriers; returns (ms, stats, launches)."""
+        h = build()
+        run_steps(h, prec, first, args.warmup)
+        h.close()
+        torch.cuda.synchronize()
+        barrier(pg, local)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        h = build()
+        st = run_steps(h, prec, first + args.warmup, args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(pg, local)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        return ms, st, h
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms64, st64, h = timed(B.FP64, 0)
+    clk = clocks.stop()
+    ms64 = max_over_ranks(pg, ms64, dev)
+    value = world * args.steps * elems_per_step / (ms64 / 1e3)
+    # launches in the timed region: the handle was built inside it, so its counter holds them all
+    launches = h.launch_count()
+
+    # roofline of the dominant kernel: the W_vvvv ladder GEMM of the EA sigma (FP64), timed live
+    D = h.dims()["dim_ea"]
+    x = torch.randn((N, D), dtype=torch.complex128, device=dev)
+    y = torch.empty_like(x)
+    B.sigma_profile(h, B.EA, 0, x, y, prec=B.FP64, stream=stream)          # plan + warm-up
+    prof = B.sigma_profile(h, B.EA, 0, x, y, prec=B.FP64, stream=stream)
+    sig_ms = sum(p[1] for p in prof)
+    sig_fl = sum(p[2] for p in prof)
+    top = max(prof, key=lambda p: p[1])
+    achieved = top[2] / (top[1] / 1e3) / 1e12
+    roof = {"bound": "alu", "kernel": f"zgemm_kernel<double> ({top[0]})", "achieved": round(achieved, 4),
+            "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
+            "traffic": None, "launch_ms": round(top[1], 4),
+            "algorithmic_flops_per_launch": top[2],
+            "peak_basis": "FP64 SIMT: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (derived, of nominal)"}
+    tfile = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    if os.path.exists(tfile):
+        try:
+            tinfo = json.load(open(tfile))
+            if tinfo.get("kernel_step") == top[0] and tinfo.get("precision") == "fp64":
+                roof["traffic"] = tinfo.get("dram_bytes_per_launch")
+                roof["traffic_source"] = tinfo.get("source")
+        except (OSError, ValueError):
+            pass
+    h.close()
+
+    out = {"metric": METRIC, "value": round(value, 3), "unit": "G elements/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms64 / args.steps, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 (complex128)",
+           "data": "synthetic (seeded; shapes of the Si 2x2x2 workload)",
+           "config": {"workload": args.workload, "kmesh": list(s.kmesh), "nocc": s.nocc, "nvir": s.nvir,
+                      "naux": s.naux, "eta": s.eta, "omega_grid": [float(s.omega[0]), float(s.omega[-1]), nomega],
+                      "omega_per_step": 1, "sectors": "ip+ea", "tol": TOL, "form": "plain fp64",
+                      "timed": "1 intermediate build + K frequency steps",
+                      "l2": "inputs larger than L2 (W_vvvv 1.9 GB, Krylov basis ~1 GB)",
+                      "parallelism": f"replicas x{world} (frequency points sharded)"},
+           "roofline": roof,
+           "sigma": {"precision": "fp64", "sector": "ea", "nvec": N, "ms": round(sig_ms, 3),
+                     "tflops": round(sig_fl / (sig_ms / 1e3) / 1e12, 4),
+                     "frac_of_fp64_peak": round(sig_fl / (sig_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS, 4)},
+           "gpu_launches": launches, "clocks": clk,
+           "solver": {"inner_iterations": sum(int(x["inner_iterations"]) for x in st64),
+                      "fp64_sigma_calls": sum(int(x["fp64_sigma_calls"]) for x in st64),
+                      "max_rel_residual": max(float(x["max_rel_residual"]) for x in st64)}}
+
+    if not args.no_chosen:
+        ms32, st32, h32 = timed(B.FP32, 0)
+        ms32 = max_over_ranks(pg, ms32, dev)
+        v32 = world * args.steps * elems_per_step / (ms32 / 1e3)
+        D = h32.dims()["dim_ea"]
+        x = torch.randn((N, D), dtype=torch.complex128, device=dev)
+        y = torch.empty_like(x)
+        B.sigma_profile(h32, B.EA, 0, x, y, prec=B.FP32, stream=stream)
+        prof32 = B.sigma_profile(h32, B.EA, 0, x, y, prec=B.FP32, stream=stream)
+        s32_ms = sum(p[1] for p in prof32)
+        s32_fl = sum(p[2] for p in prof32)
+        h32.close()
+        out["chosen_form"] = {"form": "FP32 sigma inside FP64 refinement (FP64 Krylov basis, FP64 true residual)",
+                              "value": round(v32, 3), "unit": "G elements/s", "ms_per_step": round(ms32 / args.steps, 3),
+                              "ratio_vs_plain_fp64": round(v32 / value, 3),
+                              "max_rel_residual": max(float(x["max_rel_residual"]) for x in st32),
+                              "fp64_sigma_calls": sum(int(x["fp64_sigma_calls"]) for x in st32),
+                              "lowp_sigma_calls": sum(int(x["lowp_sigma_calls"]) for x in st32),
+                              "sigma_fp32_tflops": round(s32_fl / (s32_ms / 1e3) / 1e12, 3),
+                              "sigma_fp32_frac_of_fp32_peak": round(s32_fl / (s32_ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS, 4)}
+
+    if not args.no_e2e:
+        # end to end through the public API with host buffers: H2D of the inputs from pinned memory,
+        # build, solve, D2H of G, inside the timed region (one step)
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        hL, ht1, ht2, heps = pin(s.L), pin(s.t1), pin(s.t2), pin(s.mo_energy)
+        Gh = torch.zeros((nk, 1, N, N), dtype=torch.complex128).pin_memory()
+        h_in = sum(int(t.numel() * t.element_size()) for t in (hL, ht1, ht2, heps)) + 8
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        he = B.build_intermediates(s.kmesh, s.nocc, s.nvir, s.naux, heps, hL, ht1, ht2, stream=stream)
+        opt = B.default_options(prec=B.FP64, tol=TOL, restart_m=40, max_iter=4000, max_refine=40)
+        B.solve_gf(he, B.BOTH, omega_for(args.warmup + args.steps), s.eta, Gh, options=opt, stream=stream)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        he.close()
+        te = max_over_ranks(pg, te, dev)
+        out["e2e"] = {"value": round(world * elems_per_step / te, 3), "unit": "G elements/s",
+                      "h2d_bytes_per_step": h_in, "d2h_bytes_per_step": int(Gh.numel() * Gh.element_size()),
+                      "what": "build_intermediates from pinned host arrays + solve_gf of one frequency with G to host"}
+
+    if rank == 0 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(s, omega_for(0))
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- oracle (CPU) arm
+def oracle_build(s):
+    from oracle.kccsd import KEOM
+    t0 = time.perf_counter()
+    ke = KEOM(s.kmesh, s.nocc, s.mo_energy, s.t1, s.t2, L=s.L)
+    return ke, time.perf_counter() - t0
+
+
+def oracle_sample(s, ke, omega, orbitals):
+    """GMRES (same tolerance, the oracle's own diagonal preconditioner) of one IP and one EA
+    right-hand side at k = 0 per orbital; returns the per-right-hand-side times."""
+    from oracle.kccsd import diag_estimate
+    from oracle import solvers
+    om = float(omega)
+    t_ip, t_ea = [], []
+    for p in orbitals:
+        for kind in ("ip", "ea"):
+            z = om - 1j * s.eta if kind == "ip" else om + 1j * s.eta
+            sgn = 1.0 if kind == "ip" else -1.0
+            d = diag_estimate(ke, kind, 0)
+            sig = ke.sigma_ip if kind == "ip" else ke.sigma_ea
+            b = ke.rhs_ip(0, p) if kind == "ip" else ke.rhs_ea(0, p)
+            t1 = time.perf_counter()
+            solvers.gmres(lambda x: z * x + sgn * sig(0, x), b, tol=TOL, restart=40,
+                          precond=lambda v: v / (z + sgn * d))
+            (t_ip if kind == "ip" else t_ea).append(time.perf_counter() - t1)
+    return t_ip, t_ea
+
+
+def oracle_rate(s, t_build, t_ip, t_ea):
+    """G elements/s of a step (nk * nmo right-hand sides per sector) with the build amortised over the grid."""
+    nrhs = s.nk * s.nmo
+    t_step = nrhs * (float(np.mean(t_ip)) + float(np.mean(t_ea))) + t_build / len(s.omega)
+    return s.nk * s.nmo * s.nmo / t_step, t_step
+
+
+def cpu_baseline(s, omega):
+    """The CPU oracle as it stands, timed on the host cores on a bounded sample of one step:
+    its one-time build, then one IP and one EA right-hand side (k = 0, HOMO and LUMO) at the
+    step's frequency, extrapolated to the step's right-hand sides."""
+    t0 = time.perf_counter()
+    ke, t_build = oracle_build(s)
+    t_ip, t_ea = oracle_sample(s, ke, omega[0], [s.nocc - 1])
+    v, t_step = oracle_rate(s, t_build, t_ip, t_ea)
+    return {"value": round(v, 4), "unit": "G elements/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"oracle build {t_build:.1f} s (amortised over {len(s.omega)} frequencies) + GMRES to rel. "
+                       f"residual {TOL:g} of 1 IP ({np.mean(t_ip):.2f} s) and 1 EA ({np.mean(t_ea):.2f} s) right-hand "
+                       f"side at k=0, w={float(omega[0]):.4f}, extrapolated to the step's {s.nk * s.nmo} + "
+                       f"{s.nk * s.nmo} right-hand sides ({t_step:.0f} s per step); numpy, default BLAS threads"),
+            "seconds_measured": round(time.perf_counter() - t0, 1)}
+
+
+def reference_arm(args):
+    """The oracle as the reference arm: build once, then per step one IP + one EA right-hand side
+    (orbital cycling over HOMO, LUMO, ...) at that step's frequency, rate extrapolated per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2208_07478_gb300.synth import make_workload
+    s = make_workload(args.workload)
+    t_all = time.perf_counter()
+    ke, t_build = oracle_build(s)
+    orbs = [s.nocc - 1, s.nocc, 0, s.nmo - 1]
+    rates, steps_ms = [], []
+    for k in range(args.warmup + args.steps):
+        t_ip, t_ea = oracle_sample(s, ke, s.omega[k % len(s.omega)], [orbs[k % len(orbs)]])
+        v, t_step = oracle_rate(s, t_build, t_ip, t_ea)
+        if k >= args.warmup:
+            rates.append(v)
+            steps_ms.append(t_step * 1e3)
+    v = float(np.mean(rates))
+    sample = (f"oracle build {t_build:.1f} s amortised over {len(s.omega)} frequencies; per step GMRES to rel. "
+              f"residual {TOL:g} of 1 IP + 1 EA right-hand side at k=0 (orbitals cycling HOMO, LUMO, ...), "
+              f"extrapolated to the step's {s.nk * s.nmo} + {s.nk * s.nmo} right-hand sides")
+    out = {"metric": METRIC, "value": round(v, 4), "unit": "G elements/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(float(np.mean(steps_ms)), 1),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64 (complex128)",
+           "data": "synthetic (seeded; shapes of the Si 2x2x2 workload)", "impl": "reference",
+           "config": {"workload": args.workload, "kmesh": list(s.kmesh), "nocc": s.nocc, "nvir": s.nvir,
+                      "naux": s.naux, "eta": s.eta, "omega_per_step": 1, "sectors": "ip+ea", "tol": TOL},
+           "cpu_baseline": {"value": round(v, 4), "unit": "G elements/s", "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": round(v, 4), "unit": "G elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "seconds": round(time.perf_counter() - t_all, 1)}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

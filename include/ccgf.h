@@ -135,6 +135,23 @@ ccgf_status ccgf_solve_gf(ccgf_handle *h, int sectors, int nomega, const double 
                           double eta, const ccgf_options *opt, double *G_out, int G_on_device,
                           ccgf_stats *stats, void *stream);
 
+/* Measurement helper (no counterpart in the paper): runs one sigma call like
+ * ccgf_sigma_ip / ccgf_sigma_ea (sector = CCGF_SECTOR_IP / EA) with a CUDA event
+ * between consecutive launches of its plan, and returns per step the device time
+ * (step_ms) and the algorithmic flops (step_flops: 8 per complex multiply-add of
+ * the contraction, no padding) for up to max_steps steps; *nsteps receives the
+ * number of plan steps. Synchronises the stream. Arrays are host memory owned
+ * by the caller. Errors as ccgf_sigma_ip. */
+ccgf_status ccgf_sigma_profile(ccgf_handle *h, int sector, int kshift, long long nvec, const double *x,
+                               double *y, ccgf_precision prec, void *stream, int max_steps,
+                               double *step_ms, double *step_flops, int *nsteps);
+/* Label of plan step `step` of the (sector, kshift) sigma plan built by a previous
+ * call with the current nvec ("" when absent). The string is owned by the library. */
+const char *ccgf_sigma_step_name(const ccgf_handle *h, int sector, int kshift, int step);
+
+/* Number of kernels this handle has launched since it was built (build included). */
+long long ccgf_launch_count(const ccgf_handle *h);
+
 void ccgf_destroy(ccgf_handle *h);
 const char *ccgf_status_string(ccgf_status s);
 const char *ccgf_last_error(void);

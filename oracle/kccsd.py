@@ -100,8 +100,8 @@ class KEOM:
         for k in range(nk):
             for kj in range(nk):
                 # J: (p k q k | j kj j kj), K: (p k j kj | j kj q k)
-                h[k] -= 2.0 * np.einsum('pqjj->pq', g[k, k, kj][:, :, :o, :o])
-                h[k] += np.einsum('pjjq->pq', g[k, kj, kj][:, :o, :o, :])
+                h[k] -= 2.0 * np.einsum('pqjj->pq', g[k, k, kj][:, :, :o, :o], optimize=True)
+                h[k] += np.einsum('pjjq->pq', g[k, kj, kj][:, :o, :o, :], optimize=True)
         gd = np.zeros_like(g)
         for k1 in range(nk):
             for k2 in range(nk):
@@ -113,8 +113,8 @@ class KEOM:
         for k in range(nk):
             fd[k] = X[k] @ h[k] @ Y[k]
             for kj in range(nk):
-                fd[k] += 2.0 * np.einsum('pqjj->pq', gd[k, k, kj][:, :, :o, :o])
-                fd[k] -= np.einsum('pjjq->pq', gd[k, kj, kj][:, :o, :o, :])
+                fd[k] += 2.0 * np.einsum('pqjj->pq', gd[k, k, kj][:, :, :o, :o], optimize=True)
+                fd[k] -= np.einsum('pjjq->pq', gd[k, kj, kj][:, :o, :o, :], optimize=True)
         self.g = gd
         self.f = fd
 
@@ -140,7 +140,7 @@ class KEOM:
                     kf = km.c(k, ke, kn)
                     mnef = P(k, kn, ke)[O, O, V, V]
                     mnfe = P(k, kn, kf)[O, O, V, V].transpose(0, 1, 3, 2)
-                    acc += np.einsum('mnef,inef->mi', 2 * mnef - mnfe, t[k, kn, ke])
+                    acc += np.einsum('mnef,inef->mi', 2 * mnef - mnfe, t[k, kn, ke], optimize=True)
             Foo.append(acc)
             acc = fv[k].copy()
             for kmm in range(nk):
@@ -149,7 +149,7 @@ class KEOM:
                     ke = k
                     mnef = P(kmm, kn, ke)[O, O, V, V]
                     mnfe = P(kmm, kn, kf)[O, O, V, V].transpose(0, 1, 3, 2)
-                    acc -= np.einsum('mnef,mnaf->ae', 2 * mnef - mnfe, t[kmm, kn, k])
+                    acc -= np.einsum('mnef,mnaf->ae', 2 * mnef - mnfe, t[kmm, kn, k], optimize=True)
             Fvv.append(acc)
         self.Foo, self.Fvv = Foo, Fvv
 
@@ -167,13 +167,13 @@ class KEOM:
                     w = P(k1, k2, k3)[O, O, O, O].copy()
                     for ke in range(nk):
                         kf = km.c(k1, ke, k2)
-                        w += np.einsum('mnef,ijef->mnij', P(k1, k2, ke)[O, O, V, V], t[k3, k4, ke])
+                        w += np.einsum('mnef,ijef->mnij', P(k1, k2, ke)[O, O, V, V], t[k3, k4, ke], optimize=True)
                     Woooo[k1, k2, k3] = w
                     # Wvvvv[ka,kb,ke][a,b,e,f]
                     w = P(k1, k2, k3)[V, V, V, V].copy()
                     for kmm in range(nk):
                         kn = km.c(k1, kmm, k2)
-                        w += np.einsum('mnef,mnab->abef', P(kmm, kn, k3)[O, O, V, V], t[kmm, kn, k1])
+                        w += np.einsum('mnef,mnab->abef', P(kmm, kn, k3)[O, O, V, V], t[kmm, kn, k1], optimize=True)
                     Wvvvv[k1, k2, k3] = w
                     # Wovvo[km,kb,ke][m,b,e,j], kj = km + kb - ke
                     kmm, kb, ke, kj = k1, k2, k3, k4
@@ -182,8 +182,8 @@ class KEOM:
                         kf = km.c(kmm, ke, kn)
                         mnef = P(kmm, kn, ke)[O, O, V, V]
                         mnfe = P(kmm, kn, kf)[O, O, V, V].transpose(0, 1, 3, 2)
-                        w += np.einsum('mnef,jnbf->mbej', 2 * mnef - mnfe, t[kj, kn, kb])
-                        w -= np.einsum('mnef,jnfb->mbej', mnef, t[kj, kn, kf])
+                        w += np.einsum('mnef,jnbf->mbej', 2 * mnef - mnfe, t[kj, kn, kb], optimize=True)
+                        w -= np.einsum('mnef,jnfb->mbej', mnef, t[kj, kn, kf], optimize=True)
                     Wovvo[k1, k2, k3] = w
                     # Wovov[km,kb,kj][m,b,j,e], ke = km + kb - kj
                     kmm, kb, kj, ke = k1, k2, k3, k4
@@ -191,7 +191,7 @@ class KEOM:
                     for kn in range(nk):
                         kf = km.c(kmm, ke, kn)
                         mnfe = P(kmm, kn, kf)[O, O, V, V]
-                        w -= np.einsum('mnfe,jnfb->mbje', mnfe, t[kj, kn, kf])
+                        w -= np.einsum('mnfe,jnfb->mbje', mnfe, t[kj, kn, kf], optimize=True)
                     Wovov[k1, k2, k3] = w
                     Wooov[k1, k2, k3] = P(k1, k2, k3)[O, O, O, V]
                     Wvovv[k1, k2, k3] = P(k1, k2, k3)[V, O, V, V]
@@ -199,32 +199,32 @@ class KEOM:
                     kmm, kb, ki, kj = k1, k2, k3, k4
                     w = P(kmm, kb, ki)[O, V, O, O].copy()
                     for ke in range(nk):
-                        w += np.einsum('mbef,ijef->mbij', P(kmm, kb, ke)[O, V, V, V], t[ki, kj, ke])
-                    w += np.einsum('me,ijeb->mbij', fov[kmm], t[ki, kj, kmm])
+                        w += np.einsum('mbef,ijef->mbij', P(kmm, kb, ke)[O, V, V, V], t[ki, kj, ke], optimize=True)
+                    w += np.einsum('me,ijeb->mbij', fov[kmm], t[ki, kj, kmm], optimize=True)
                     for kn in range(nk):
                         ke = km.c(kmm, ki, kn)
                         mnie = P(kmm, kn, ki)[O, O, O, V]
                         mnei = P(kmm, kn, ke)[O, O, V, O].transpose(0, 1, 3, 2)
-                        w += np.einsum('mnie,jnbe->mbij', 2 * mnie - mnei, t[kj, kn, kb])
-                        w -= np.einsum('mnie,jneb->mbij', mnie, t[kj, kn, ke])
+                        w += np.einsum('mnie,jnbe->mbij', 2 * mnie - mnei, t[kj, kn, kb], optimize=True)
+                        w -= np.einsum('mnie,jneb->mbij', mnie, t[kj, kn, ke], optimize=True)
                         ke2 = km.c(kmm, kj, kn)
-                        w -= np.einsum('mnej,ineb->mbij', P(kmm, kn, ke2)[O, O, V, O], t[ki, kn, ke2])
+                        w -= np.einsum('mnej,ineb->mbij', P(kmm, kn, ke2)[O, O, V, O], t[ki, kn, ke2], optimize=True)
                     Wovoo[k1, k2, k3] = w
                     # Wvvvo[ka,kb,ke][a,b,e,j], kj = ka + kb - ke
                     ka, kb, ke, kj = k1, k2, k3, k4
                     w = P(ka, kb, ke)[V, V, V, O].copy()
                     for kmm in range(nk):
                         kn = km.c(ka, kmm, kb)
-                        w += np.einsum('mnej,mnab->abej', P(kmm, kn, ke)[O, O, V, O], t[kmm, kn, ka])
-                    w -= np.einsum('me,mjab->abej', fov[ke], t[ke, kj, ka])
+                        w += np.einsum('mnej,mnab->abej', P(kmm, kn, ke)[O, O, V, O], t[kmm, kn, ka], optimize=True)
+                    w -= np.einsum('me,mjab->abej', fov[ke], t[ke, kj, ka], optimize=True)
                     for kmm in range(nk):
                         kf = km.c(kmm, ka, kj)
-                        w -= np.einsum('mbef,mjaf->abej', P(kmm, kb, ke)[O, V, V, V], t[kmm, kj, ka])
+                        w -= np.einsum('mbef,mjaf->abej', P(kmm, kb, ke)[O, V, V, V], t[kmm, kj, ka], optimize=True)
                         kf2 = km.c(kmm, ke, ka)
                         maef = P(kmm, ka, ke)[O, V, V, V]
                         mafe = P(kmm, ka, kf2)[O, V, V, V].transpose(0, 1, 3, 2)
-                        w += np.einsum('maef,mjfb->abej', 2 * mafe - maef, t[kmm, kj, kf2])
-                        w -= np.einsum('maef,mjbf->abej', mafe, t[kmm, kj, kb])
+                        w += np.einsum('maef,mjfb->abej', 2 * mafe - maef, t[kmm, kj, kf2], optimize=True)
+                        w -= np.einsum('maef,mjbf->abej', mafe, t[kmm, kj, kb], optimize=True)
                     Wvvvo[k1, k2, k3] = w
         self.Woooo, self.Wvvvv = Woooo, Wvvvv
         self.Wovvo, self.Wovov = Wovvo, Wovov
@@ -258,12 +258,12 @@ class KEOM:
         r1, r2 = self.ip_unpack(x)
         s1 = -self.Foo[K].T @ r1
         for kmm in range(nk):
-            s1 += np.einsum('me,ime->i', self.Fov[kmm], 2 * r2[K, kmm] - r2[kmm, K].transpose(1, 0, 2))
+            s1 += np.einsum('me,ime->i', self.Fov[kmm], 2 * r2[K, kmm] - r2[kmm, K].transpose(1, 0, 2), optimize=True)
             for kn in range(nk):
                 ke = km.c(kmm, K, kn)
                 mnie = P(kmm, kn, K)[O, O, O, V]
                 mnei = P(kmm, kn, ke)[O, O, V, O].transpose(0, 1, 3, 2)
-                s1 -= np.einsum('mnie,mne->i', 2 * mnie - mnei, r2[kmm, kn])
+                s1 -= np.einsum('mnie,mne->i', 2 * mnie - mnei, r2[kmm, kn], optimize=True)
         s2 = np.zeros_like(r2)
         # three-body intermediate X[e], k_e = K
         X = np.zeros(self.nvir, dtype=np.complex128)
@@ -272,23 +272,23 @@ class KEOM:
                 kf = km.c(kmm, K, kn)
                 mnef = P(kmm, kn, K)[O, O, V, V]
                 mnfe = P(kmm, kn, kf)[O, O, V, V].transpose(0, 1, 3, 2)
-                X += np.einsum('mnef,mnf->e', 2 * mnef - mnfe, r2[kmm, kn])
+                X += np.einsum('mnef,mnf->e', 2 * mnef - mnfe, r2[kmm, kn], optimize=True)
         for ki in range(nk):
             for kj in range(nk):
                 ka = km.c(ki, K, kj)
-                acc = -np.einsum('maij,m->ija', self.Wovoo[K, ka, ki], r1)
-                acc += np.einsum('ae,ije->ija', self.Fvv[ka], r2[ki, kj])
-                acc -= np.einsum('mi,mja->ija', self.Foo[ki], r2[ki, kj])
-                acc -= np.einsum('mj,ima->ija', self.Foo[kj], r2[ki, kj])
+                acc = -np.einsum('maij,m->ija', self.Wovoo[K, ka, ki], r1, optimize=True)
+                acc += np.einsum('ae,ije->ija', self.Fvv[ka], r2[ki, kj], optimize=True)
+                acc -= np.einsum('mi,mja->ija', self.Foo[ki], r2[ki, kj], optimize=True)
+                acc -= np.einsum('mj,ima->ija', self.Foo[kj], r2[ki, kj], optimize=True)
                 for kmm in range(nk):
                     kn = km.c(ki, kmm, kj)
-                    acc += np.einsum('mnij,mna->ija', self.Woooo[kmm, kn, ki], r2[kmm, kn])
-                    acc -= np.einsum('maie,mje->ija', self.Wovov[kmm, ka, ki], r2[kmm, kj])
+                    acc += np.einsum('mnij,mna->ija', self.Woooo[kmm, kn, ki], r2[kmm, kn], optimize=True)
+                    acc -= np.einsum('maie,mje->ija', self.Wovov[kmm, ka, ki], r2[kmm, kj], optimize=True)
                     ke = km.c(ki, K, kmm)
                     acc += np.einsum('maej,ime->ija', self.Wovvo[kmm, ka, ke],
-                                     2 * r2[ki, kmm] - r2[kmm, ki].transpose(1, 0, 2))
-                    acc -= np.einsum('maje,ime->ija', self.Wovov[kmm, ka, kj], r2[ki, kmm])
-                acc -= np.einsum('e,ijea->ija', X, t[ki, kj, K])
+                                     2 * r2[ki, kmm] - r2[kmm, ki].transpose(1, 0, 2), optimize=True)
+                    acc -= np.einsum('maje,ime->ija', self.Wovov[kmm, ka, kj], r2[ki, kmm], optimize=True)
+                acc -= np.einsum('e,ijea->ija', X, t[ki, kj, K], optimize=True)
                 s2[ki, kj] = acc
         return self.pack(s1, s2)
 
@@ -300,37 +300,37 @@ class KEOM:
         r1, r2 = self.ea_unpack(x)
         s1 = self.Fvv[K] @ r1
         for kmm in range(nk):
-            s1 += np.einsum('me,mae->a', self.Fov[kmm], 2 * r2[kmm, K] - r2[kmm, kmm].transpose(0, 2, 1))
+            s1 += np.einsum('me,mae->a', self.Fov[kmm], 2 * r2[kmm, K] - r2[kmm, kmm].transpose(0, 2, 1), optimize=True)
             for ke in range(nk):
                 kf = km.c(K, ke, kmm)
                 amef = P(K, kmm, ke)[V, O, V, V]
                 amfe = P(K, kmm, kf)[V, O, V, V].transpose(0, 1, 3, 2)
-                s1 += np.einsum('amef,mef->a', 2 * amef - amfe, r2[kmm, ke])
+                s1 += np.einsum('amef,mef->a', 2 * amef - amfe, r2[kmm, ke], optimize=True)
         Y = np.zeros(self.nocc, dtype=np.complex128)
         for kn in range(nk):
             for ke in range(nk):
                 kf = km.c(K, ke, kn)
                 mnef = P(K, kn, ke)[O, O, V, V]
                 mnfe = P(K, kn, kf)[O, O, V, V].transpose(0, 1, 3, 2)
-                Y += np.einsum('mnef,nef->m', 2 * mnef - mnfe, r2[kn, ke])
+                Y += np.einsum('mnef,nef->m', 2 * mnef - mnfe, r2[kn, ke], optimize=True)
         s2 = np.zeros_like(r2)
         for kj in range(nk):
             for ka in range(nk):
                 kb = km.c(K, ka, kj)
-                acc = np.einsum('abej,e->jab', self.Wvvvo[ka, kb, K], r1)
-                acc += np.einsum('ae,jeb->jab', self.Fvv[ka], r2[kj, ka])
-                acc += np.einsum('be,jae->jab', self.Fvv[kb], r2[kj, ka])
-                acc -= np.einsum('mj,mab->jab', self.Foo[kj], r2[kj, ka])
+                acc = np.einsum('abej,e->jab', self.Wvvvo[ka, kb, K], r1, optimize=True)
+                acc += np.einsum('ae,jeb->jab', self.Fvv[ka], r2[kj, ka], optimize=True)
+                acc += np.einsum('be,jae->jab', self.Fvv[kb], r2[kj, ka], optimize=True)
+                acc -= np.einsum('mj,mab->jab', self.Foo[kj], r2[kj, ka], optimize=True)
                 for kmm in range(nk):
                     ke = km.c(K, ka, kmm)
                     acc += np.einsum('mbej,mae->jab', self.Wovvo[kmm, kb, ke],
-                                     2 * r2[kmm, ka] - r2[kmm, ke].transpose(0, 2, 1))
-                    acc -= np.einsum('mbje,mae->jab', self.Wovov[kmm, kb, kj], r2[kmm, ka])
+                                     2 * r2[kmm, ka] - r2[kmm, ke].transpose(0, 2, 1), optimize=True)
+                    acc -= np.einsum('mbje,mae->jab', self.Wovov[kmm, kb, kj], r2[kmm, ka], optimize=True)
                     ke2 = km.c(kmm, kj, ka)
-                    acc -= np.einsum('maje,meb->jab', self.Wovov[kmm, ka, kj], r2[kmm, ke2])
+                    acc -= np.einsum('maje,meb->jab', self.Wovov[kmm, ka, kj], r2[kmm, ke2], optimize=True)
                 for ke in range(nk):
-                    acc += np.einsum('abef,jef->jab', self.Wvvvv[ka, kb, ke], r2[kj, ke])
-                acc -= np.einsum('m,mjab->jab', Y, t[K, kj, ka])
+                    acc += np.einsum('abef,jef->jab', self.Wvvvv[ka, kb, ke], r2[kj, ke], optimize=True)
+                acc -= np.einsum('m,mjab->jab', Y, t[K, kj, ka], optimize=True)
                 s2[kj, ka] = acc
         return self.pack(s1, s2)
 
@@ -369,7 +369,7 @@ class KEOM:
                 for kc in range(nk):
                     kd = km.c(K, kc, kl)
                     tt = 2 * t[K, kl, kc][k] - t[K, kl, kd][k].transpose(0, 2, 1)
-                    e1 -= np.einsum('lcd,ilcd->i', tt, l2[K, kl, kc])
+                    e1 -= np.einsum('lcd,ilcd->i', tt, l2[K, kl, kc], optimize=True)
             for kj in range(nk):
                 e2[K, kj][k, :, :] += 2 * l1[kj]
             for ki in range(nk):
@@ -415,7 +415,7 @@ class KEOM:
                 for kl in range(nk):
                     kd = km.c(kk, K, kl)
                     ll = 2 * l2[kk, kl, K] - l2[kl, kk, K].transpose(1, 0, 2, 3)
-                    e1 -= np.einsum('kld,klad->a', t[kk, kl, K][:, :, c, :], ll)
+                    e1 -= np.einsum('kld,klad->a', t[kk, kl, K][:, :, c, :], ll, optimize=True)
             for kj in range(nk):
                 # k_a = K term, then k_b = K term (k_a = kj)
                 e2[kj, K][:, c, :] += 2 * l1[kj]
@@ -438,3 +438,27 @@ class KEOM:
     def diagonal(self, kind, K):
         """Exact diagonal of the EOM matrix (by unit vectors; tiny systems only)."""
         return np.diag(self.matrix(kind, K)).copy()
+
+
+def diag_estimate(ke, kind, K):
+    """One-body part of diag(A) at total momentum K (a preconditioner; it does not change the solution).
+
+    IP: r1[i] -> -Foo_ii,  r2[ki,kj][i,j,a] -> Fvv_aa - Foo_ii - Foo_jj;
+    EA: r1[a] -> Fvv_aa,   r2[kj,ka][j,a,b] -> Fvv_aa + Fvv_bb - Foo_jj.
+    """
+    km, nk, o, v = ke.km, ke.nk, ke.nocc, ke.nvir
+    foo = [np.real(np.diag(ke.Foo[k])) for k in range(nk)]
+    fvv = [np.real(np.diag(ke.Fvv[k])) for k in range(nk)]
+    if kind == "ip":
+        d2 = np.zeros((nk, nk, o, o, v))
+        for ki in range(nk):
+            for kj in range(nk):
+                ka = km.c(ki, K, kj)
+                d2[ki, kj] = fvv[ka][None, None, :] - foo[ki][:, None, None] - foo[kj][None, :, None]
+        return np.concatenate([-foo[K], d2.ravel()])
+    d2 = np.zeros((nk, nk, o, v, v))
+    for kj in range(nk):
+        for ka in range(nk):
+            kb = km.c(K, ka, kj)
+            d2[kj, ka] = fvv[ka][None, :, None] + fvv[kb][None, None, :] - foo[kj][:, None, None]
+    return np.concatenate([fvv[K], d2.ravel()])

@@ -43,7 +43,8 @@ class Stats(C.Structure):
 
 
 EXPORTS = ["ccgf_default_options", "ccgf_build_intermediates", "ccgf_dims", "ccgf_sigma_ip", "ccgf_sigma_ea",
-           "ccgf_rhs", "ccgf_left", "ccgf_solve_gf", "ccgf_destroy", "ccgf_status_string", "ccgf_last_error"]
+           "ccgf_rhs", "ccgf_left", "ccgf_solve_gf", "ccgf_sigma_profile", "ccgf_sigma_step_name", "ccgf_launch_count", "ccgf_destroy",
+           "ccgf_status_string", "ccgf_last_error"]
 
 _lib = None
 
@@ -72,6 +73,12 @@ def load(path: str | None = None):
         getattr(lib, name).restype = i
     lib.ccgf_solve_gf.argtypes = [vp, i, i, vp, d, C.POINTER(Options), vp, i, C.POINTER(Stats), vp]
     lib.ccgf_solve_gf.restype = i
+    lib.ccgf_sigma_profile.argtypes = [vp, i, i, ll, vp, vp, i, vp, i, C.POINTER(d), C.POINTER(d), C.POINTER(i)]
+    lib.ccgf_sigma_profile.restype = i
+    lib.ccgf_sigma_step_name.argtypes = [vp, i, i, i]
+    lib.ccgf_sigma_step_name.restype = C.c_char_p
+    lib.ccgf_launch_count.argtypes = [vp]
+    lib.ccgf_launch_count.restype = ll
     lib.ccgf_destroy.argtypes = [vp]
     lib.ccgf_destroy.restype = None
     lib.ccgf_status_string.argtypes = [i]
@@ -142,6 +149,9 @@ class Handle:
         except Exception:
             pass
 
+    def launch_count(self):
+        return int(load().ccgf_launch_count(self.ptr))
+
     def dims(self):
         nk, o, v = C.c_int(), C.c_int(), C.c_int()
         dip, dea = C.c_longlong(), C.c_longlong()
@@ -175,6 +185,18 @@ def sigma_ip(h: Handle, kshift, x, y, prec=FP64, stream=None):
 def sigma_ea(h: Handle, kshift, x, y, prec=FP64, stream=None):
     nvec = x.shape[0] if x.ndim == 2 else 1
     return _check(load().ccgf_sigma_ea(h.ptr, kshift, nvec, _ptr(x), _ptr(y), prec, _stream_ptr(stream)))
+
+
+def sigma_profile(h: Handle, sector, kshift, x, y, prec=FP64, stream=None, max_steps=64):
+    """One sigma call with per-step device times; returns [(name, ms, flops)]."""
+    nvec = x.shape[0] if x.ndim == 2 else 1
+    ms = (C.c_double * max_steps)()
+    fl = (C.c_double * max_steps)()
+    n = C.c_int()
+    lib = load()
+    _check(lib.ccgf_sigma_profile(h.ptr, sector, kshift, nvec, _ptr(x), _ptr(y), prec, _stream_ptr(stream), max_steps,
+                                  ms, fl, C.byref(n)))
+    return [(lib.ccgf_sigma_step_name(h.ptr, sector, kshift, k).decode(), ms[k], fl[k]) for k in range(min(n.value, max_steps))]
 
 
 def rhs(h: Handle, sector, K, p, out, stream=None):

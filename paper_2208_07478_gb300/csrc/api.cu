@@ -2,6 +2,7 @@
 #include "ccgf_internal.h"
 #include <cmath>
 #include <new>
+#include <vector>
 
 namespace {
 
@@ -102,12 +103,14 @@ ccgf_status ccgf_build_intermediates(const ccgf_system *sys, const ccgf_options 
     } else {
         if ((s = dalloc(h->l1, nk * o * v)) != CCGF_OK) return fail(s);
         conj_kernel<<<256, 256, 0, st>>>(h->t1.p, h->l1.p, h->l1.n);
+        h->launches++;
     }
     if (sys->l2) {
         if ((s = copy_in(h->l2, sys->l2, h->t2.n, dev, st)) != CCGF_OK) return fail(s);
     } else {
         if ((s = dalloc(h->l2, h->t2.n)) != CCGF_OK) return fail(s);
         conj_kernel<<<1024, 256, 0, st>>>(h->t2.p, h->l2.p, h->l2.n);
+        h->launches++;
     }
     if ((s = build_intermediates(h, sys, st)) != CCGF_OK) return fail(s);
     *out = h;
@@ -185,6 +188,38 @@ ccgf_status ccgf_solve_gf(ccgf_handle *h, int sectors, int nomega, const double 
     if (o.prec != CCGF_FP64 && o.prec != CCGF_FP32) { set_last_error("unknown precision"); return CCGF_ERR_INVALID_ARG; }
     return solve_gf(h, sectors, nomega, omega, eta, &o, G_out, G_on_device, stats, (cudaStream_t)stream);
 }
+
+ccgf_status ccgf_sigma_profile(ccgf_handle *h, int sector, int kshift, long long nvec, const double *x, double *y,
+                               ccgf_precision prec, void *stream, int max_steps, double *step_ms, double *step_flops,
+                               int *nsteps) {
+    if (!h || !step_ms || !step_flops || !nsteps || max_steps < 1) { set_last_error("NULL output or max_steps < 1"); return CCGF_ERR_INVALID_ARG; }
+    if (sector != CCGF_SECTOR_IP && sector != CCGF_SECTOR_EA) { set_last_error("sector must be IP or EA"); return CCGF_ERR_INVALID_ARG; }
+    std::vector<cudaEvent_t> ev(max_steps + 1);
+    for (auto &e : ev) CCGF_CUDA_TRY(cudaEventCreate(&e));
+    h->prof_events = ev.data();
+    h->prof_max = max_steps + 1;
+    h->prof_count = 0;
+    ccgf_status s = sigma_abi(h, sector, kshift, nvec, x, y, prec, stream);
+    h->prof_events = nullptr;
+    int n = plan_step_count(h, sector, kshift);
+    *nsteps = n;
+    if (s == CCGF_OK) {
+        for (int i = 0; i < n && i < max_steps; ++i) {
+            float ms = 0.f;
+            if (i + 1 < h->prof_count) cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+            step_ms[i] = ms;
+            step_flops[i] = plan_step_flops(h, sector, kshift, i);
+        }
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    return s;
+}
+
+const char *ccgf_sigma_step_name(const ccgf_handle *h, int sector, int kshift, int step) {
+    return h ? plan_step_name(h, sector, kshift, step) : "";
+}
+
+long long ccgf_launch_count(const ccgf_handle *h) { return h ? h->launches : 0; }
 
 void ccgf_destroy(ccgf_handle *h) { destroy(h); }
 

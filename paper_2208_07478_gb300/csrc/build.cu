@@ -562,8 +562,10 @@ ccgf_status build_intermediates(ccgf_handle *h, const ccgf_system *sys, cudaStre
         if (!W[b].p) continue;
         CCGF_TRY(dalloc(h->Wf[b], W[b].n));
         to_float_kernel<<<grid_for(W[b].n), 256, 0, st>>>(W[b].p, h->Wf[b].p, W[b].n);
+        h->launches++;
     }
     CCGF_CUDA_TRY(cudaGetLastError());
+    h->launches += 22;   // the fixed kernels of this function (finite checks, dressing, ERIs, blocks)
     CCGF_CUDA_TRY(cudaStreamSynchronize(st));
     dfree(g);
     dfree(Ld);

@@ -54,9 +54,14 @@ struct GemmDesc {
     const i64 *offA, *offB, *offC;   // device offset tables
     double2 alpha, beta;
 };
+// Long-K GEMMs with few output tiles split K across CTAs (deterministic: partial sums go to
+// `work`, then one reduction applies alpha / beta); work may be NULL (no split).
+int zgemm_ksplit(const GemmDesc &d);
+i64 zgemm_workspace_elems(const GemmDesc &d);
+// returns the number of kernels launched
 template <typename R>
-void launch_zgemm(const GemmDesc &d, const typename cvec<R>::T *A, const typename cvec<R>::T *B,
-                  typename cvec<R>::T *C, cudaStream_t st);
+int launch_zgemm(const GemmDesc &d, const typename cvec<R>::T *A, const typename cvec<R>::T *B,
+                 typename cvec<R>::T *C, cudaStream_t st, typename cvec<R>::T *work = nullptr, i64 work_elems = 0);
 
 // ----------------------------------------------------------------------------- batched permute
 // C[offC[b] + sum_d i_d sC_d] = alpha * A[offA[b] + sum_d i_d sA_d] + beta * C[...]
@@ -70,7 +75,7 @@ struct PermDesc {
     double2 alpha, beta;
 };
 template <typename R>
-void launch_zpermute(const PermDesc &d, const typename cvec<R>::T *A, typename cvec<R>::T *C, cudaStream_t st);
+int launch_zpermute(const PermDesc &d, const typename cvec<R>::T *A, typename cvec<R>::T *C, cudaStream_t st);
 
 // ----------------------------------------------------------------------------- k-mesh
 struct KMeshH {
@@ -89,6 +94,7 @@ struct KMeshH {
 // (the input vector is copied there first), C operands are the output or scratch.
 enum { STEP_GEMM = 0, STEP_PERM = 1, STEP_FOV_IP = 2, STEP_FOV_EA = 3 };
 struct SigmaStep {
+    const char *name;
     int kind;
     GemmDesc g;
     PermDesc p;
@@ -102,7 +108,7 @@ struct SigmaPlan {
     DBuf<i64> offsets;
     std::vector<i64> host_off;
     i64 scratch_elems;
-    i64 seg[8];        // scratch segment offsets (complex elements)
+    i64 seg[12];       // scratch segment offsets (complex elements)
 };
 
 enum {
@@ -133,11 +139,17 @@ struct ccgf_handle {
     std::vector<SigmaPlan *> plans;
     int plan_nv = 0;
     i64 launches = 0;
+    // optional per-step timing of one sigma call (ccgf_sigma_profile)
+    cudaEvent_t *prof_events = nullptr;
+    int prof_max = 0, prof_count = 0;
 };
 
 // build.cu
 ccgf_status build_intermediates(ccgf_handle *h, const ccgf_system *sys, cudaStream_t st);
 // sigma.cu
+double plan_step_flops(const ccgf_handle *h, int sector, int K, int step);   // algorithmic flops of a plan step
+int plan_step_count(const ccgf_handle *h, int sector, int K);
+const char *plan_step_name(const ccgf_handle *h, int sector, int K, int step);
 ccgf_status sigma_apply(ccgf_handle *h, int sector, int K, int nv, const double2 *x, double2 *y,
                         ccgf_precision prec, cudaStream_t st);
 void free_plans(ccgf_handle *h);

@@ -60,7 +60,8 @@ template <typename T, typename S> __device__ __forceinline__ void cfma(T &acc, c
 template <typename R>
 __global__ void __launch_bounds__(256) zgemm_kernel(GemmDesc d, const typename cvec<R>::T *__restrict__ A,
                                                     const typename cvec<R>::T *__restrict__ B,
-                                                    typename cvec<R>::T *__restrict__ C) {
+                                                    typename cvec<R>::T *__restrict__ C, int ksplit, int kchunk,
+                                                    typename cvec<R>::T *__restrict__ work) {
     typedef typename cvec<R>::T T;
     constexpr int BM = 64, BN = 64, BK = 16;
     __shared__ T As[BK][BM];
@@ -70,7 +71,9 @@ __global__ void __launch_bounds__(256) zgemm_kernel(GemmDesc d, const typename c
     const T alpha = {(R)d.alpha.x, (R)d.alpha.y};
     const T beta = {(R)d.beta.x, (R)d.beta.y};
     const bool use_beta = (d.beta.x != 0.0 || d.beta.y != 0.0);
-    for (int b = blockIdx.z; b < d.batch; b += gridDim.z) {
+    for (int bz = blockIdx.z; bz < d.batch * ksplit; bz += gridDim.z) {
+        const int b = bz / ksplit, ks = bz % ksplit;
+        const int kbeg = ks * kchunk, kend = min(d.K, kbeg + kchunk);
         T acc[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
@@ -79,20 +82,20 @@ __global__ void __launch_bounds__(256) zgemm_kernel(GemmDesc d, const typename c
         for (int r = 0; r < d.nred; ++r) {
             const T *Ab = A + d.offA[(i64)b * d.nred + r];
             const T *Bb = B + d.offB[(i64)b * d.nred + r];
-            for (int k0 = 0; k0 < d.K; k0 += BK) {
+            for (int k0 = kbeg; k0 < kend; k0 += BK) {
 #pragma unroll
                 for (int s = 0; s < 4; ++s) {
                     int l = tid + 256 * s, i, kk;
                     if (d.csA == 1) { kk = l & 15; i = l >> 4; } else { i = l & 63; kk = l >> 6; }
                     int m = m0 + i, k = k0 + kk;
-                    As[kk][i] = (m < d.M && k < d.K) ? Ab[(i64)m * d.rsA + (i64)k * d.csA] : cz<T>();
+                    As[kk][i] = (m < d.M && k < kend) ? Ab[(i64)m * d.rsA + (i64)k * d.csA] : cz<T>();
                 }
 #pragma unroll
                 for (int s = 0; s < 4; ++s) {
                     int l = tid + 256 * s, nn, kk;
                     if (d.csB == 1) { nn = l & 63; kk = l >> 6; } else { kk = l & 15; nn = l >> 4; }
                     int n = n0 + nn, k = k0 + kk;
-                    Bs[kk][nn] = (n < d.N && k < d.K) ? Bb[(i64)k * d.rsB + (i64)n * d.csB] : cz<T>();
+                    Bs[kk][nn] = (n < d.N && k < kend) ? Bb[(i64)k * d.rsB + (i64)n * d.csB] : cz<T>();
                 }
                 __syncthreads();
 #pragma unroll
@@ -109,6 +112,21 @@ __global__ void __launch_bounds__(256) zgemm_kernel(GemmDesc d, const typename c
                 }
                 __syncthreads();
             }
+        }
+        if (ksplit > 1) {
+            // raw partial sums to work[b][ks][M][N]; zgemm_splitk_reduce applies alpha and beta
+            T *Wb = work + ((i64)b * ksplit + ks) * (i64)d.M * d.N;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                int m = m0 + ty + 16 * i;
+                if (m >= d.M) continue;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    int n = n0 + tx + 16 * j;
+                    if (n < d.N) Wb[(i64)m * d.N + n] = acc[i][j];
+                }
+            }
+            continue;
         }
         T *Cb = C + d.offC[b];
 #pragma unroll
@@ -135,14 +153,72 @@ __global__ void __launch_bounds__(256) zgemm_kernel(GemmDesc d, const typename c
 }
 
 template <typename R>
-void launch_zgemm(const GemmDesc &d, const typename cvec<R>::T *A, const typename cvec<R>::T *B,
-                  typename cvec<R>::T *C, cudaStream_t st) {
-    if (d.batch <= 0 || d.M <= 0 || d.N <= 0) return;
-    dim3 grid((unsigned)ceil_div(d.N, 64), (unsigned)ceil_div(d.M, 64), (unsigned)(d.batch < 65535 ? d.batch : 65535));
-    zgemm_kernel<R><<<grid, 256, 0, st>>>(d, A, B, C);
+__global__ void zgemm_splitk_reduce(GemmDesc d, int ksplit, const typename cvec<R>::T *__restrict__ work,
+                                    typename cvec<R>::T *__restrict__ C) {
+    typedef typename cvec<R>::T T;
+    const i64 mn = (i64)d.M * d.N;
+    const bool use_beta = (d.beta.x != 0.0 || d.beta.y != 0.0);
+    for (i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x; t < mn * d.batch; t += (i64)gridDim.x * blockDim.x) {
+        const int b = (int)(t / mn);
+        const i64 e = t - (i64)b * mn;
+        const int m = (int)(e / d.N), n = (int)(e - (i64)m * d.N);
+        R sx = 0, sy = 0;
+        for (int s = 0; s < ksplit; ++s) {
+            T p = work[((i64)b * ksplit + s) * mn + e];
+            sx += p.x;
+            sy += p.y;
+        }
+        T *c = C + d.offC[b] + (i64)m * d.rsC + (i64)n * d.csC;
+        T v;
+        v.x = (R)d.alpha.x * sx - (R)d.alpha.y * sy;
+        v.y = (R)d.alpha.x * sy + (R)d.alpha.y * sx;
+        if (use_beta) {
+            T o = *c;
+            v.x += (R)d.beta.x * o.x - (R)d.beta.y * o.y;
+            v.y += (R)d.beta.x * o.y + (R)d.beta.y * o.x;
+        }
+        *c = v;
+    }
 }
-template void launch_zgemm<double>(const GemmDesc &, const double2 *, const double2 *, double2 *, cudaStream_t);
-template void launch_zgemm<float>(const GemmDesc &, const float2 *, const float2 *, float2 *, cudaStream_t);
+
+int zgemm_ksplit(const GemmDesc &d) {
+    // Enough CTAs to cover the SMs twice; every split keeps at least 8 k-tiles of work.
+    const i64 tiles = ceil_div(d.M, 64) * ceil_div(d.N, 64) * (i64)d.batch;
+    if (tiles >= 304 || d.nred != 1) return 1;
+    i64 s = ceil_div(304, tiles);
+    i64 smax = d.K / 128;
+    if (s > smax) s = smax;
+    return (int)(s < 1 ? 1 : s);
+}
+i64 zgemm_workspace_elems(const GemmDesc &d) {
+    int s = zgemm_ksplit(d);
+    return s > 1 ? (i64)s * d.M * d.N * d.batch : 0;
+}
+
+template <typename R>
+int launch_zgemm(const GemmDesc &d, const typename cvec<R>::T *A, const typename cvec<R>::T *B,
+                 typename cvec<R>::T *C, cudaStream_t st, typename cvec<R>::T *work, i64 work_elems) {
+    if (d.batch <= 0 || d.M <= 0 || d.N <= 0) return 0;
+    int ks = zgemm_ksplit(d);
+    if (ks > 1 && (work == nullptr || work_elems < zgemm_workspace_elems(d))) ks = 1;
+    int kchunk = d.K;
+    if (ks > 1) {
+        kchunk = (int)(ceil_div(ceil_div(d.K, ks), 16) * 16);
+        ks = (int)ceil_div(d.K, kchunk);
+    }
+    i64 z = (i64)d.batch * ks;
+    dim3 grid((unsigned)ceil_div(d.N, 64), (unsigned)ceil_div(d.M, 64), (unsigned)(z < 65535 ? z : 65535));
+    zgemm_kernel<R><<<grid, 256, 0, st>>>(d, A, B, C, ks, kchunk, work);
+    if (ks > 1) {
+        i64 n = (i64)d.M * d.N * d.batch;
+        i64 g = ceil_div(n, 256);
+        zgemm_splitk_reduce<R><<<(unsigned)(g > 4096 ? 4096 : g), 256, 0, st>>>(d, ks, work, C);
+        return 2;
+    }
+    return 1;
+}
+template int launch_zgemm<double>(const GemmDesc &, const double2 *, const double2 *, double2 *, cudaStream_t, double2 *, i64);
+template int launch_zgemm<float>(const GemmDesc &, const float2 *, const float2 *, float2 *, cudaStream_t, float2 *, i64);
 
 // ----------------------------------------------------------------------------- batched permute-add
 template <typename R>
@@ -175,15 +251,16 @@ __global__ void zpermute_kernel(PermDesc d, const typename cvec<R>::T *__restric
 }
 
 template <typename R>
-void launch_zpermute(const PermDesc &d, const typename cvec<R>::T *A, typename cvec<R>::T *C, cudaStream_t st) {
-    if (d.batch <= 0 || d.total <= 0) return;
+int launch_zpermute(const PermDesc &d, const typename cvec<R>::T *A, typename cvec<R>::T *C, cudaStream_t st) {
+    if (d.batch <= 0 || d.total <= 0) return 0;
     i64 gx = ceil_div(d.total, 256);
     if (gx > 4096) gx = 4096;
     dim3 grid((unsigned)gx, (unsigned)(d.batch < 65535 ? d.batch : 65535));
     zpermute_kernel<R><<<grid, 256, 0, st>>>(d, A, C);
+    return 1;
 }
-template void launch_zpermute<double>(const PermDesc &, const double2 *, double2 *, cudaStream_t);
-template void launch_zpermute<float>(const PermDesc &, const float2 *, float2 *, cudaStream_t);
+template int launch_zpermute<double>(const PermDesc &, const double2 *, double2 *, cudaStream_t);
+template int launch_zpermute<float>(const PermDesc &, const float2 *, float2 *, cudaStream_t);
 
 // ----------------------------------------------------------------------------- ABI <-> internal layout
 // x: [nvec][D] (ABI), xt: [D][nv] (internal, columns >= nvec zero-filled)

@@ -24,6 +24,7 @@ namespace {
 struct PlanBuilder {
     SigmaPlan *P;
     std::vector<i64> off;   // host copy of the offset table
+    const char *cur = "";   // label of the term being emitted
 
     i64 push(const std::vector<i64> &v) {
         i64 pos = (i64)off.size();
@@ -33,6 +34,7 @@ struct PlanBuilder {
     void gemm(int M, int N, int K, int nred, int a_buf, i64 rsA, i64 csA, const std::vector<i64> &oA, i64 rsB, i64 csB,
               const std::vector<i64> &oB, int c_buf, i64 rsC, i64 csC, const std::vector<i64> &oC, double alpha, double beta) {
         SigmaStep s{};
+        s.name = cur;
         s.kind = STEP_GEMM;
         s.g.M = M;
         s.g.N = N;
@@ -58,6 +60,7 @@ struct PlanBuilder {
     void perm(std::vector<i64> dims, std::vector<i64> sA, const std::vector<i64> &oA, int c_buf, std::vector<i64> sC,
               const std::vector<i64> &oC, double alpha, double beta) {
         SigmaStep s{};
+        s.name = cur;
         s.kind = STEP_PERM;
         s.p.nd = (int)dims.size();
         s.p.total = 1;
@@ -78,18 +81,21 @@ struct PlanBuilder {
     }
     void fov(int kind) {
         SigmaStep s{};
+        s.name = kind == STEP_FOV_IP ? "ip_fov" : "ea_fov";
         s.kind = kind;
         P->steps.push_back(s);
     }
 };
 
-enum { SEG_X = 0, SEG_R, SEG_Q, SEG_T1, SEG_T3, SEG_XT, SEG_SMALL, SEG_END };
+enum { SEG_X = 0, SEG_R, SEG_Q, SEG_T1, SEG_T3, SEG_XT, SEG_SMALL, SEG_SPLITK, SEG_END };
 
-void scratch_layout(const ccgf_handle *h, int nv, i64 seg[8]) {
+void scratch_layout(const ccgf_handle *h, int nv, i64 seg[SEG_END + 1]) {
     const i64 nk2 = (i64)h->nk * h->nk, o = h->o, v = h->v;
     i64 dmax = h->dim_ip > h->dim_ea ? h->dim_ip : h->dim_ea;
     i64 r2max = nk2 * o * v * (o > v ? o : v);
-    i64 sizes[SEG_END] = {dmax * nv, r2max * nv, r2max * nv, r2max * nv, r2max * nv, r2max * nv, (o + v) * (i64)nv};
+    // split-K partials: at most 304 slices of an (o+v) x nv product
+    i64 sizes[SEG_END] = {dmax * nv, r2max * nv, r2max * nv, r2max * nv, r2max * nv, r2max * nv, (o + v) * (i64)nv,
+                          304 * (o + v) * (i64)nv};
     i64 pos = 0;
     for (int s = 0; s < SEG_END; ++s) {
         seg[s] = pos;
@@ -114,12 +120,15 @@ SigmaPlan *build_plan_ea(const ccgf_handle *h, int K, int nv) {
     const i64 v2 = (i64)v * v, ov = (i64)o * v, nk2 = (i64)nk * nk;
 
     // s1[a] = Fvv[K] r1 (first write)
+    B.cur = "ea_s1_fvv";
     B.gemm(v, nv, v, 1, BUF_FVV, v, 1, {(i64)K * v2}, NV, 1, {sx}, BUF_Y, NV, 1, {0}, 1.0, 0.0);
     B.fov(STEP_FOV_EA);
     // s1 += sum (2<am|ef> - <am|fe>) r2
+    B.cur = "ea_s1_vovv";
     B.gemm(v, nv, (int)(nk2 * o * v2), 1, BUF_UVOVV, nk2 * o * v2, 1, {(i64)K * v * nk2 * o * v2}, NV, 1, {sx + v * NV},
            BUF_Y, NV, 1, {0}, 1.0, 1.0);
     // s2 = Wvvvo r1 (first write of every block)
+    B.cur = "ea_s2_wvvvo";
     {
         std::vector<i64> oA, oB, oC;
         for (int kj = 0; kj < nk; ++kj)
@@ -132,6 +141,7 @@ SigmaPlan *build_plan_ea(const ccgf_handle *h, int K, int nv) {
         B.gemm((int)(o * v2), nv, v, 1, BUF_WVVVO, v, 1, oA, NV, 1, oB, BUF_Y, NV, 1, oC, 1.0, 0.0);
     }
     // s2 += Fvv[ka](a,e) r2[j,e,b]
+    B.cur = "ea_s2_fvv_a";
     {
         std::vector<i64> oA, oB, oC;
         for (int kj = 0; kj < nk; ++kj)
@@ -144,6 +154,7 @@ SigmaPlan *build_plan_ea(const ccgf_handle *h, int K, int nv) {
         B.gemm(v, (int)(v * NV), v, 1, BUF_FVV, v, 1, oA, v * NV, 1, oB, BUF_Y, v * NV, 1, oC, 1.0, 1.0);
     }
     // s2 += Fvv[kb](b,e) r2[j,a,e]
+    B.cur = "ea_s2_fvv_b";
     {
         std::vector<i64> oA, oB, oC;
         for (int kj = 0; kj < nk; ++kj)
@@ -160,6 +171,7 @@ SigmaPlan *build_plan_ea(const ccgf_handle *h, int K, int nv) {
         B.gemm(v, nv, v, 1, BUF_FVV, v, 1, oA, NV, 1, oB, BUF_Y, NV, 1, oC, 1.0, 1.0);
     }
     // s2 -= Foo[kj](m,j) r2[m,a,b]
+    B.cur = "ea_s2_foo";
     {
         std::vector<i64> oA, oB, oC;
         for (int kj = 0; kj < nk; ++kj)
@@ -171,6 +183,7 @@ SigmaPlan *build_plan_ea(const ccgf_handle *h, int K, int nv) {
         B.gemm(o, (int)(v2 * NV), o, 1, BUF_FOO, 1, o, oA, v2 * NV, 1, oB, BUF_Y, v2 * NV, 1, oC, -1.0, 1.0);
     }
     // R'[ka][km][m][e][a] = r2[km,ka][m,a,e]
+    B.cur = "ea_ring_gather";
     {
         std::vector<i64> oA, oC;
         for (int ka = 0; ka < nk; ++ka)
@@ -181,6 +194,7 @@ SigmaPlan *build_plan_ea(const ccgf_handle *h, int K, int nv) {
         B.perm({o, v, v, NV}, {v2 * NV, NV, v * NV, 1}, oA, BUF_SCRATCH, {v2 * NV, v * NV, NV, 1}, oC, 1.0, 0.0);
     }
     // ring: T1[kj][ka][j][b][a] = sum_km W1[kb][kj][km] R'[ka][km] + W2[kb][kj][km] Q'[ka][km], Q' = r2[km,ke][m,e,a]
+    B.cur = "ea_ring_w1w2";
     {
         std::vector<i64> oA, oB, oC;
         const i64 blk = ov * ov;
@@ -207,6 +221,7 @@ SigmaPlan *build_plan_ea(const ccgf_handle *h, int K, int nv) {
         B.perm({o, v, v, NV}, {v2 * NV, v * NV, NV, 1}, pA, BUF_Y, {v2 * NV, NV, v * NV, 1}, pC, 1.0, 1.0);
     }
     // ring: s2[j,a,b] += sum_km WN[ka][kj][km](j,a;m,e) r2[km,ke2][m,e,b], ke2 = km + ka - kj
+    B.cur = "ea_ring_wn";
     {
         std::vector<i64> oA, oB, oC;
         const i64 blk = ov * ov;
@@ -222,6 +237,7 @@ SigmaPlan *build_plan_ea(const ccgf_handle *h, int K, int nv) {
         B.gemm((int)ov, (int)(v * NV), (int)ov, nk, BUF_WOV3, ov, 1, oA, v * NV, 1, oB, BUF_Y, v * NV, 1, oC, 1.0, 1.0);
     }
     // ladder: XT[kj][ke][e][f][j] = r2[kj,ke][j,e,f];  T3[kj][ka][a][b][j] = Wvvvv[ka,kb] XT[kj];  s2 += T3
+    B.cur = "ea_ladder_wvvvv";
     {
         std::vector<i64> oA, oC;
         for (int kj = 0; kj < nk; ++kj)
@@ -249,6 +265,7 @@ SigmaPlan *build_plan_ea(const ccgf_handle *h, int K, int nv) {
         B.perm({v, v, o, NV}, {v * o * NV, o * NV, NV, 1}, pA, BUF_Y, {v * NV, NV, v2 * NV, 1}, pC, 1.0, 1.0);
     }
     // three-body: Ysm[m] = sum (2<mn|ef> - <mn|fe>) r2[kn,ke][n,e,f];  s2 -= t2[K,kj,ka][m,j,a,b] Ysm[m]
+    B.cur = "ea_threebody";
     {
         const i64 sm = P->seg[SEG_SMALL];
         B.gemm(o, nv, (int)(nk2 * o * v2), 1, BUF_UOOVV_EA, nk2 * o * v2, 1, {(i64)K * o * nk2 * o * v2}, NV, 1,
@@ -282,12 +299,15 @@ SigmaPlan *build_plan_ip(const ccgf_handle *h, int K, int nv) {
     const i64 o2 = (i64)o * o, ov = (i64)o * v, nk2 = (i64)nk * nk;
 
     // s1 = -Foo[K]^T r1
+    B.cur = "ip_s1_foo";
     B.gemm(o, nv, o, 1, BUF_FOO, 1, o, {(i64)K * o2}, NV, 1, {sx}, BUF_Y, NV, 1, {0}, -1.0, 0.0);
     B.fov(STEP_FOV_IP);
     // s1 -= sum (2<mn|ie> - <mn|ei>) r2
+    B.cur = "ip_s1_ooov";
     B.gemm(o, nv, (int)(nk2 * S2), 1, BUF_UOOOV, nk2 * S2, 1, {(i64)K * o * nk2 * S2}, NV, 1, {sx + o * NV}, BUF_Y, NV, 1,
            {0}, -1.0, 1.0);
     // s2 = -Wovoo r1 (first write)
+    B.cur = "ip_s2_wovoo";
     {
         std::vector<i64> oA, oB, oC;
         for (int ki = 0; ki < nk; ++ki)
@@ -299,6 +319,7 @@ SigmaPlan *build_plan_ip(const ccgf_handle *h, int K, int nv) {
         B.gemm((int)S2, nv, o, 1, BUF_WOVOO, o, 1, oA, NV, 1, oB, BUF_Y, NV, 1, oC, -1.0, 0.0);
     }
     // s2 += Fvv[ka](a,e) r2[i,j,e]
+    B.cur = "ip_s2_fvv";
     {
         std::vector<i64> oA, oB, oC;
         for (int ki = 0; ki < nk; ++ki)
@@ -314,6 +335,7 @@ SigmaPlan *build_plan_ip(const ccgf_handle *h, int K, int nv) {
         B.gemm(v, nv, v, 1, BUF_FVV, v, 1, oA, NV, 1, oB, BUF_Y, NV, 1, oC, 1.0, 1.0);
     }
     // s2 -= Foo[ki](m,i) r2[m,j,a]
+    B.cur = "ip_s2_foo_i";
     {
         std::vector<i64> oA, oB, oC;
         for (int ki = 0; ki < nk; ++ki)
@@ -325,6 +347,7 @@ SigmaPlan *build_plan_ip(const ccgf_handle *h, int K, int nv) {
         B.gemm(o, (int)(ov * NV), o, 1, BUF_FOO, 1, o, oA, ov * NV, 1, oB, BUF_Y, ov * NV, 1, oC, -1.0, 1.0);
     }
     // s2 -= Foo[kj](m,j) r2[i,m,a]
+    B.cur = "ip_s2_foo_j";
     {
         std::vector<i64> oA, oB, oC;
         for (int ki = 0; ki < nk; ++ki)
@@ -337,6 +360,7 @@ SigmaPlan *build_plan_ip(const ccgf_handle *h, int K, int nv) {
         B.gemm(o, (int)(v * NV), o, 1, BUF_FOO, 1, o, oA, v * NV, 1, oB, BUF_Y, v * NV, 1, oC, -1.0, 1.0);
     }
     // s2 += sum_km Woooo[ki][kj](i,j;km,m,n) r2[km,kn][m,n,a]
+    B.cur = "ip_ladder_woooo";
     {
         std::vector<i64> oA, oB, oC;
         for (int ki = 0; ki < nk; ++ki)
@@ -351,6 +375,7 @@ SigmaPlan *build_plan_ip(const ccgf_handle *h, int K, int nv) {
         B.gemm((int)o2, (int)(v * NV), (int)o2, nk, BUF_WOOOO, nk * o2, 1, oA, v * NV, 1, oB, BUF_Y, v * NV, 1, oC, 1.0, 1.0);
     }
     // R'[ki][km][m][e][i] = r2[ki,km][i,m,e];  Q'[kj][km][m][e][j] = r2[km,kj][m,j,e]
+    B.cur = "ip_ring_gather";
     {
         std::vector<i64> oA, oC;
         for (int ki = 0; ki < nk; ++ki)
@@ -369,6 +394,7 @@ SigmaPlan *build_plan_ip(const ccgf_handle *h, int K, int nv) {
     }
     const i64 blk = ov * ov;
     // ring: T1[ki][kj][j][a][i] = sum_km W1[ka][kj][km] R'[ki][km] + W2[ka][kj][km] Q'[ki][km]
+    B.cur = "ip_ring_w1w2";
     {
         std::vector<i64> oA, oB, oC;
         for (int ki = 0; ki < nk; ++ki)
@@ -394,6 +420,7 @@ SigmaPlan *build_plan_ip(const ccgf_handle *h, int K, int nv) {
         B.perm({o, v, o, NV}, {v * o * NV, o * NV, NV, 1}, pA, BUF_Y, {v * NV, NV, ov * NV, 1}, pC, 1.0, 1.0);
     }
     // ring: T3[ki][kj][i][a][j] = sum_km WN[ka][ki][km] Q'[kj][km]
+    B.cur = "ip_ring_wn";
     {
         std::vector<i64> oA, oB, oC;
         for (int ki = 0; ki < nk; ++ki)
@@ -416,6 +443,7 @@ SigmaPlan *build_plan_ip(const ccgf_handle *h, int K, int nv) {
         B.perm({o, v, o, NV}, {v * o * NV, o * NV, NV, 1}, pA, BUF_Y, {ov * NV, NV, v * NV, 1}, pC, 1.0, 1.0);
     }
     // three-body: Xsm[e] = sum (2<mn|ef> - <mn|fe>) r2[km,kn][m,n,f];  s2 -= t2[ki,kj,K][i,j,e,a] Xsm[e]
+    B.cur = "ip_threebody";
     {
         const i64 sm = P->seg[SEG_SMALL];
         B.gemm(v, nv, (int)(nk2 * S2), 1, BUF_UOOVV_IP, nk2 * S2, 1, {(i64)K * v * nk2 * S2}, NV, 1, {sx + o * NV},
@@ -511,7 +539,10 @@ void run_plan(ccgf_handle *h, SigmaPlan *P, const double2 *x, double2 *y, cudaSt
     convert_kernel<R><<<gsz(n), 256, 0, st>>>(x, scr + P->seg[SEG_X], n);
     h->launches++;
     const i64 *offs = P->offsets.p;
+    int si = 0;
     for (const SigmaStep &s : P->steps) {
+        if (h->prof_events && si < h->prof_max) cudaEventRecord(h->prof_events[si], st);
+        ++si;
         T *C = s.c_buf == BUF_Y ? yout : scr;
         if (s.kind == STEP_GEMM) {
             GemmDesc d = s.g;
@@ -519,21 +550,23 @@ void run_plan(ccgf_handle *h, SigmaPlan *P, const double2 *x, double2 *y, cudaSt
             d.offB = offs + s.offB_pos;
             d.offC = offs + s.offC_pos;
             const T *A = f64 ? (const T *)h->W[s.a_buf].p : (const T *)h->Wf[s.a_buf].p;
-            launch_zgemm<R>(d, A, scr, C, st);
+            h->launches += launch_zgemm<R>(d, A, scr, C, st, scr + P->seg[SEG_SPLITK], P->seg[SEG_END] - P->seg[SEG_SPLITK]);
         } else if (s.kind == STEP_PERM) {
             PermDesc d = s.p;
             d.offA = offs + s.offA_pos;
             d.offC = offs + s.offC_pos;
-            launch_zpermute<R>(d, scr, C, st);
+            h->launches += launch_zpermute<R>(d, scr, C, st);
         } else {
             const int sector = s.kind == STEP_FOV_IP ? CCGF_SECTOR_IP : CCGF_SECTOR_EA;
             const int nrow = sector == CCGF_SECTOR_IP ? h->o : h->v;
             const T *F = f64 ? (const T *)h->W[BUF_FOV].p : (const T *)h->Wf[BUF_FOV].p;
             fov_kernel<T, R><<<(unsigned)ceil_div((i64)nrow * P->nv, 128), 128, 0, st>>>(
                 sector, P->K, h->nk, h->o, h->v, P->nv, F, scr + P->seg[SEG_X], yout);
+            h->launches++;
         }
-        h->launches++;
     }
+    if (h->prof_events && si < h->prof_max) cudaEventRecord(h->prof_events[si], st);
+    h->prof_count = si + 1;
     if (!f64) {
         widen_kernel<<<gsz(n), 256, 0, st>>>(h->yf.p, y, n);
         h->launches++;
@@ -583,6 +616,31 @@ bool check_plan(const ccgf_handle *h, const SigmaPlan *P, const std::vector<i64>
 }
 
 }  // namespace
+
+static const SigmaPlan *plan_of(const ccgf_handle *h, int sector, int K) {
+    if (h->plans.empty() || K < 0 || K >= h->nk || (sector != 1 && sector != 2)) return nullptr;
+    return h->plans[(sector - 1) * h->nk + K];
+}
+int plan_step_count(const ccgf_handle *h, int sector, int K) {
+    const SigmaPlan *P = plan_of(h, sector, K);
+    return P ? (int)P->steps.size() : 0;
+}
+double plan_step_flops(const ccgf_handle *h, int sector, int K, int step) {
+    const SigmaPlan *P = plan_of(h, sector, K);
+    if (!P || step < 0 || step >= (int)P->steps.size()) return 0.0;
+    const SigmaStep &s = P->steps[step];
+    if (s.kind == STEP_GEMM) return 8.0 * s.g.M * (double)s.g.N * s.g.K * s.g.nred * s.g.batch;
+    if (s.kind == STEP_FOV_IP || s.kind == STEP_FOV_EA) {
+        double rows = s.kind == STEP_FOV_IP ? h->o : h->v;
+        return 8.0 * rows * P->nv * h->nk * h->o * h->v;
+    }
+    return 0.0;
+}
+const char *plan_step_name(const ccgf_handle *h, int sector, int K, int step) {
+    const SigmaPlan *P = plan_of(h, sector, K);
+    if (!P || step < 0 || step >= (int)P->steps.size()) return "";
+    return P->steps[step].name;
+}
 
 void free_plans(ccgf_handle *h) {
     for (SigmaPlan *p : h->plans)

@@ -334,7 +334,7 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
         const i64 D = sector == CCGF_SECTOR_IP ? h->dim_ip : h->dim_ea;
         const double s = sector == CCGF_SECTOR_IP ? 1.0 : -1.0;
         const int nvmax = N * nwc;
-        DBuf<double2> Bq, E, B, X, R, U, AU, V, Ct, Hs, Hs2, Hm, cs, sn, g, y, z;
+        DBuf<double2> Bq, E, B, X, R, U, AU, V, Ct, Hs, Hs2, Hm, cs, sn, g, y, z, Wk;
         DBuf<double> dvec, beta2, beta, hn2, target, res;
         DBuf<int> active, nunconv;
         CCGF_TRY(dalloc(Bq, D * N));
@@ -346,6 +346,7 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
         CCGF_TRY(dalloc(AU, D * nvmax));
         CCGF_TRY(dalloc(V, (i64)(m + 1) * D * nvmax));
         CCGF_TRY(dalloc(Ct, (i64)N * nvmax));
+        CCGF_TRY(dalloc(Wk, (i64)304 * N * nvmax));
         CCGF_TRY(dalloc(Hs, (i64)nvmax * (m + 1)));
         CCGF_TRY(dalloc(Hs2, (i64)nvmax * (m + 1)));
         CCGF_TRY(dalloc(Hm, (i64)nvmax * (m + 1) * m));
@@ -363,7 +364,7 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
         CCGF_TRY(dalloc(active, nvmax));
         CCGF_TRY(dalloc(nunconv, 1));
         auto free_all = [&]() {
-            DBuf<double2> *zb[] = {&Bq, &E, &B, &X, &R, &U, &AU, &V, &Ct, &Hs, &Hs2, &Hm, &cs, &sn, &g, &y, &z};
+            DBuf<double2> *zb[] = {&Bq, &E, &B, &X, &R, &U, &AU, &V, &Ct, &Hs, &Hs2, &Hm, &cs, &sn, &g, &y, &z, &Wk};
             for (auto *b : zb) dfree(*b);
             DBuf<double> *db[] = {&dvec, &beta2, &beta, &hn2, &target, &res};
             for (auto *b : db) dfree(*b);
@@ -376,6 +377,7 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                 CCGF_TRY(make_left(h, sector, K, p, E.p + (i64)p * D, 1, st));
             }
             diag_kernel<<<g1(D), 256, 0, st>>>(sector, K, nk, o, v, h->kadd_d.p, h->ksub_d.p, h->W[BUF_FOO].p, h->W[BUF_FVV].p, dvec.p, D);
+            h->launches++;
             for (int w0 = 0; w0 < nomega; w0 += nwc) {
                 const int nw = std::min(nwc, nomega - w0);
                 const int nv = N * nw;
@@ -385,6 +387,7 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                 CCGF_CUDA_TRY(cudaMemcpyAsync(z.p, zh.data(), sizeof(double2) * nv, cudaMemcpyHostToDevice, st));
                 Shift Sh{z.p, s, dvec.p};
                 expand_kernel<<<g1(Dn), 256, 0, st>>>(Bq.p, B.p, D, N, nw);
+                h->launches++;
                 CCGF_CUDA_TRY(cudaMemsetAsync(X.p, 0, sizeof(double2) * Dn, st));
                 CCGF_CUDA_TRY(cudaMemcpyAsync(R.p, B.p, sizeof(double2) * Dn, cudaMemcpyDeviceToDevice, st));
                 const i64 rpb = std::max<i64>(64, ceil_div(D, std::max<i64>(1, 2048 / (i64)ceil_div(nv, 32))));
@@ -392,6 +395,7 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                 // target = tol * ||b||
                 CCGF_CUDA_TRY(cudaMemsetAsync(beta2.p, 0, sizeof(double) * nv, st));
                 colnorm2_kernel<<<rgrid, dim3(32, 8), 0, st>>>(B.p, beta2.p, D, nv, rpb);
+                h->launches++;
                 std::vector<double> b2(nv);
                 CCGF_CUDA_TRY(cudaMemcpyAsync(b2.data(), beta2.p, sizeof(double) * nv, cudaMemcpyDeviceToHost, st));
                 CCGF_CUDA_TRY(cudaStreamSynchronize(st));
@@ -406,7 +410,9 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                     // beta = ||r||, freeze columns already below target
                     CCGF_CUDA_TRY(cudaMemsetAsync(beta2.p, 0, sizeof(double) * nv, st));
                     colnorm2_kernel<<<rgrid, dim3(32, 8), 0, st>>>(R.p, beta2.p, D, nv, rpb);
+                    h->launches++;
                     init_cycle_kernel<<<(unsigned)ceil_div(nv, 128), 128, 0, st>>>(nv, m, beta2.p, beta.p, g.p, target.p, active.p);
+                    h->launches++;
                     std::vector<double> bh(nv);
                     CCGF_CUDA_TRY(cudaMemcpyAsync(bh.data(), beta.p, sizeof(double) * nv, cudaMemcpyDeviceToHost, st));
                     CCGF_CUDA_TRY(cudaStreamSynchronize(st));
@@ -422,22 +428,27 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                     if (cycles >= opt->max_refine || it_total >= opt->max_iter) break;
                     cycles++;
                     start_kernel<<<g1(Dn), 256, 0, st>>>(R.p, V.p, beta.p, active.p, D, nv);
+                    h->launches++;
                     int J = 0;
                     for (int j = 0; j < m; ++j) {
                         double2 *Vj = V.p + (i64)j * Dn, *Vn = V.p + (i64)(j + 1) * Dn;
                         precond_kernel<<<g1(Dn), 256, 0, st>>>(Sh, Vj, U.p, D, nv);
+                        h->launches++;
                         cudaEventRecord(es0, st);
                         CCGF_TRY(sigma_apply(h, sector, K, nv, U.p, AU.p, opt->prec, st));
                         cudaEventRecord(es1, st);
                         if (opt->prec == CCGF_FP64) S.fp64_sigma_calls++; else S.lowp_sigma_calls++;
                         shift_kernel<<<g1(Dn), 256, 0, st>>>(Sh, U.p, AU.p, Vn, D, nv);
+                        h->launches++;
                         CCGF_CUDA_TRY(cudaMemsetAsync(Hs.p, 0, sizeof(double2) * nv * (m + 1), st));
                         for (int pass = 0; pass < 2; ++pass) {
                             // CGS2: accumulate both passes' coefficients in Hs, subtract each pass
                             DBuf<double2> &hp = pass == 0 ? Hs : Hs2;
                             if (pass == 1) CCGF_CUDA_TRY(cudaMemsetAsync(Hs2.p, 0, sizeof(double2) * nv * (m + 1), st));
                             cgs_dot_kernel<<<rgrid, dim3(32, 8), 0, st>>>(V.p, Dn, Vn, hp.p, m + 1, j + 1, D, nv, rpb);
+                            h->launches++;
                             cgs_axpy_kernel<<<g1(Dn), 256, 0, st>>>(V.p, Dn, Vn, hp.p, m + 1, j + 1, D, nv);
+                            h->launches++;
                         }
                         // sum the two CGS passes into Hs (small host-free kernel via permute-add)
                         {
@@ -457,32 +468,36 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                             pd.offC = zero_off.p;
                             pd.alpha = make_double2(1, 0);
                             pd.beta = make_double2(1, 0);
-                            launch_zpermute<double>(pd, Hs2.p, Hs.p, st);
+                            h->launches += launch_zpermute<double>(pd, Hs2.p, Hs.p, st);
                         }
                         CCGF_CUDA_TRY(cudaMemsetAsync(hn2.p, 0, sizeof(double) * nv, st));
                         colnorm2_kernel<<<rgrid, dim3(32, 8), 0, st>>>(Vn, hn2.p, D, nv, rpb);
+                        h->launches++;
                         CCGF_CUDA_TRY(cudaMemsetAsync(nunconv.p, 0, sizeof(int), st));
                         givens_kernel<<<(unsigned)ceil_div(nv, 128), 128, 0, st>>>(j, m, nv, Hs.p, m + 1, hn2.p, Hm.p, cs.p, sn.p, g.p,
                                                                                    target.p, active.p, res.p, nunconv.p);
+                        h->launches++;
                         normalize_kernel<<<g1(Dn), 256, 0, st>>>(Vn, hn2.p, D, nv);
+                        h->launches++;
                         CCGF_CUDA_TRY(cudaMemcpyAsync(nunconv_h, nunconv.p, sizeof(int), cudaMemcpyDeviceToHost, st));
                         CCGF_CUDA_TRY(cudaStreamSynchronize(st));
                         float ms = 0;
                         cudaEventElapsedTime(&ms, es0, es1);
                         sigma_ms += ms;
-                        h->launches += 10;
                         J = j + 1;
                         it_total++;
                         // stop the cycle a little below the target so the FP64 check passes
                         if (*nunconv_h == 0 || it_total >= opt->max_iter) break;
                     }
                     trisolve_kernel<<<(unsigned)ceil_div(nv, 128), 128, 0, st>>>(J, m, nv, Hm.p, g.p, y.p);
+                    h->launches++;
                     update_kernel<<<g1(Dn), 256, 0, st>>>(Sh, J, m, V.p, Dn, y.p, X.p, D, nv);
+                    h->launches++;
                     // true residual with the FP64 sigma (refinement step)
                     CCGF_TRY(sigma_apply(h, sector, K, nv, X.p, AU.p, CCGF_FP64, st));
                     S.fp64_sigma_calls++;
                     residual_kernel<<<g1(Dn), 256, 0, st>>>(Sh, B.p, X.p, AU.p, R.p, D, nv);
-                    h->launches += 4;
+                    h->launches++;
                 }
                 S.inner_iterations += it_total;
                 S.rhs_solved += nv;
@@ -512,9 +527,9 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                     gd.offC = zoff.p + 2;
                     gd.alpha = make_double2(1, 0);
                     gd.beta = make_double2(0, 0);
-                    launch_zgemm<double>(gd, E.p, X.p, Ct.p, st);
+                    h->launches += launch_zgemm<double>(gd, E.p, X.p, Ct.p, st, Wk.p, Wk.n);
                     scatter_g_kernel<<<g1((i64)N * nv), 256, 0, st>>>(sector, Ct.p, N, nw, nv, G, K, w0, nomega);
-                    h->launches += 2;
+                    h->launches++;
                 }
                 CCGF_CUDA_TRY(cudaGetLastError());
             }
