@@ -223,7 +223,10 @@ def gpu_arm(args):
     if os.path.exists(tfile):
         try:
             tinfo = json.load(open(tfile))
-            if tinfo.get("kernel_step") == top[0] and tinfo.get("precision") == "fp64":
+            import hashlib
+            src = open(os.path.join(ROOT, "paper_2208_07478_gb300", "csrc", "kernels.cu"), "rb").read()
+            same_kernel = tinfo.get("kernels_cu_sha256") == hashlib.sha256(src).hexdigest()
+            if same_kernel and tinfo.get("kernel_step") == top[0] and tinfo.get("precision") == "fp64":
                 roof["traffic"] = tinfo.get("dram_bytes_per_launch")
                 roof["traffic_source"] = tinfo.get("source")
         except (OSError, ValueError):

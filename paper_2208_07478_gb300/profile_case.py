@@ -1,0 +1,52 @@
+"""One sigma application on a configurable synthetic system, for profilers.
+
+    python -m paper_2208_07478_gb300.profile_case --kmesh 2 2 2 --nocc 4 --nvir 16 --sector ea --prec fp64
+
+Builds the similarity-transformed Hamiltonian blocks, then applies the EA (or
+IP) sigma of momentum 0 to nvec random vectors once (after one warm-up call
+that builds the plan). Prints the per-step device times of a profiled call.
+"""
+import argparse
+import os
+import sys
+
+import numpy as np
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--kmesh", type=int, nargs=3, default=[2, 2, 2])
+    ap.add_argument("--nocc", type=int, default=4)
+    ap.add_argument("--nvir", type=int, default=16)
+    ap.add_argument("--naux", type=int, default=64)
+    ap.add_argument("--nvec", type=int, default=0, help="default: nocc + nvir")
+    ap.add_argument("--sector", default="ea", choices=["ip", "ea"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--calls", type=int, default=1)
+    a = ap.parse_args()
+    import torch
+    from paper_2208_07478_gb300 import binding as B
+    from paper_2208_07478_gb300.synth import make_system
+    s = make_system(tuple(a.kmesh), a.nocc, a.nvir, a.naux, seed=1, L_sigma=0.05, t1_sigma=0.01, nomega=0)
+    h = B.build_intermediates(s.kmesh, s.nocc, s.nvir, s.naux, s.mo_energy, s.L, s.t1, s.t2)
+    d = h.dims()
+    D = d["dim_ea"] if a.sector == "ea" else d["dim_ip"]
+    nvec = a.nvec or s.nmo
+    x = torch.randn((nvec, D), dtype=torch.complex128, device="cuda")
+    y = torch.empty_like(x)
+    prec = B.FP64 if a.prec == "fp64" else B.FP32
+    fn = B.sigma_ea if a.sector == "ea" else B.sigma_ip
+    fn(h, 0, x, y, prec=prec)
+    for _ in range(a.calls):
+        fn(h, 0, x, y, prec=prec)
+    torch.cuda.synchronize()
+    prof = B.sigma_profile(h, B.EA if a.sector == "ea" else B.IP, 0, x, y, prec=prec)
+    for name, ms, fl in prof:
+        print(f"{name:20s} {ms:9.3f} ms  {fl / 1e9:10.3f} GFLOP  {fl / max(ms, 1e-9) / 1e9:8.3f} TFLOP/s")
+    h.close()
+
+
+if __name__ == "__main__":
+    main()
