@@ -76,13 +76,19 @@ def barrier(pg, device=None):
             pg.barrier()
 
 
-def max_over_ranks(pg, x, device):
+def max_over_ranks(pg, x, device=None):
+    """Largest value over the ranks (device None: a CPU tensor, for the gloo backend)."""
     if pg is None:
         return x
     import torch
     t = torch.tensor([x], dtype=torch.float64, device=device)
     pg.all_reduce(t, op=pg.ReduceOp.MAX)
     return float(t.item())
+
+
+def omega_index(rank, world, step, nomega):
+    """Frequency point of (rank, step): a rank-strided walk over the grid, so ranks never share a point."""
+    return (rank + world * step) % nomega
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -159,8 +165,7 @@ def gpu_arm(args):
     Gd = torch.zeros((nk, 1, N, N), dtype=torch.complex128, device=dev)
 
     def omega_for(step):
-        # rank-strided walk over the frequency grid: ranks never share a point
-        return s.omega[[(rank + world * step) % nomega]]
+        return s.omega[[omega_index(rank, world, step, nomega)]]
 
     def build():
         return B.build_intermediates(s.kmesh, s.nocc, s.nvir, s.naux, deps, dL, dt1, dt2, on_device=True, stream=stream)

@@ -153,6 +153,9 @@ const char *plan_step_name(const ccgf_handle *h, int sector, int K, int step);
 ccgf_status sigma_apply(ccgf_handle *h, int sector, int K, int nv, const double2 *x, double2 *y,
                         ccgf_precision prec, cudaStream_t st);
 void free_plans(ccgf_handle *h);
+ccgf_status sigma_apply_in_arena(ccgf_handle *h, int sector, int K, int nv, const double2 *x, double2 *y, double2 *arena,
+                                 i64 arena_elems, i64 *offsets, i64 offsets_cap, cudaStream_t st);
+i64 sigma_arena_elems(const ccgf_handle *h, int nv);
 // vectors.cu
 ccgf_status make_rhs(ccgf_handle *h, int sector, int K, int p, double2 *out, i64 ld, cudaStream_t st);
 ccgf_status make_left(ccgf_handle *h, int sector, int K, int p, double2 *out, i64 ld, cudaStream_t st);

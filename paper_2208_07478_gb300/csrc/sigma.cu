@@ -509,6 +509,8 @@ __global__ void fov_kernel(int sector, int K, int nk, int o, int v, int nv, cons
     y[(i64)p * nv + c] = out;
 }
 
+template <typename R> using T_arena = typename cvec<R>::T *;
+
 template <typename R>
 __global__ void convert_kernel(const double2 *__restrict__ a, typename cvec<R>::T *__restrict__ b, i64 n) {
     for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
@@ -528,10 +530,10 @@ inline unsigned gsz(i64 n) {
 }
 
 template <typename R>
-void run_plan(ccgf_handle *h, SigmaPlan *P, const double2 *x, double2 *y, cudaStream_t st) {
+void run_plan(ccgf_handle *h, SigmaPlan *P, const double2 *x, double2 *y, cudaStream_t st, T_arena<R> arena = nullptr) {
     typedef typename cvec<R>::T T;
     const bool f64 = sizeof(R) == 8;
-    T *scr = f64 ? (T *)h->scratch.p : (T *)h->scratch_f.p;
+    T *scr = arena ? arena : (f64 ? (T *)h->scratch.p : (T *)h->scratch_f.p);
     const i64 D = P->sector == CCGF_SECTOR_IP ? h->dim_ip : h->dim_ea;
     const i64 n = D * P->nv;
     T *yout = f64 ? (T *)y : (T *)h->yf.p;
@@ -699,4 +701,43 @@ ccgf_status sigma_apply(ccgf_handle *h, int sector, int K, int nv, const double2
     }
     CCGF_CUDA_TRY(cudaGetLastError());
     return CCGF_OK;
+}
+
+// Sigma with caller-provided device workspace: the plan is built on the host only,
+// its offset table is copied into `offsets` (capacity in entries) and every scratch
+// segment lives in `arena` (capacity in complex elements). No device allocation.
+ccgf_status sigma_apply_in_arena(ccgf_handle *h, int sector, int K, int nv, const double2 *x, double2 *y, double2 *arena,
+                                 i64 arena_elems, i64 *offsets, i64 offsets_cap, cudaStream_t st) {
+    SigmaPlan *P = sector == CCGF_SECTOR_IP ? build_plan_ip(h, K, nv) : build_plan_ea(h, K, nv);
+    if (P->scratch_elems > arena_elems || (i64)P->host_off.size() > offsets_cap) {
+        i64 need = P->scratch_elems, noff = (i64)P->host_off.size();
+        delete P;
+        set_last_error("workspace too small for this nvec: needs " + std::to_string(need) + " complex elements and " +
+                       std::to_string(noff) + " offsets");
+        return CCGF_ERR_INVALID_ARG;
+    }
+    std::string why;
+    if (!check_plan(h, P, P->host_off, why)) {
+        delete P;
+        set_last_error("internal sigma plan failed its bound check: " + why);
+        return CCGF_ERR_INVALID_ARG;
+    }
+    cudaError_t e = cudaMemcpyAsync(offsets, P->host_off.data(), sizeof(i64) * P->host_off.size(), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+        delete P;
+        set_last_error(std::string("offset table copy: ") + cudaGetErrorString(e));
+        return CCGF_ERR_CUDA;
+    }
+    P->offsets.p = offsets;   // borrowed, not owned
+    run_plan<double>(h, P, x, y, st, arena);
+    P->offsets.p = nullptr;
+    delete P;
+    CCGF_CUDA_TRY(cudaGetLastError());
+    return CCGF_OK;
+}
+
+i64 sigma_arena_elems(const ccgf_handle *h, int nv) {
+    i64 seg[SEG_END + 1];
+    scratch_layout(h, nv, seg);
+    return seg[SEG_END];
 }
