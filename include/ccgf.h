@@ -149,6 +149,20 @@ ccgf_status ccgf_sigma_profile(ccgf_handle *h, int sector, int kshift, long long
  * call with the current nvec ("" when absent). The string is owned by the library. */
 const char *ccgf_sigma_step_name(const ccgf_handle *h, int sector, int kshift, int step);
 
+/* ccgf_sigma_ip without device allocation (no counterpart in the paper): the same
+ * FP64 EOM-IP sigma, for callers that must not call cudaMalloc during a call (a host
+ * framework that owns all device memory through its own pool, a latency-critical
+ * loop that cannot afford the synchronisation an allocation may imply, a process
+ * whose device memory is already fully reserved). All scratch lives in one static
+ * device array of 32 MiB per device (held until the process exits); a (dim_ip, nvec)
+ * that does not fit returns CCGF_ERR_INVALID_ARG with the size it would need. The
+ * first call on a device looks up the array's address (make it before any stream
+ * capture). Calls share the array: calls whose kernels overlap on the GPU race, so
+ * order them. x, y: device complex [nvec][dim_ip], as ccgf_sigma_ip; stream-ordered,
+ * does not synchronise. */
+ccgf_status ccgf_sigma_ip_noalloc(ccgf_handle *h, int kshift, long long nvec, const double *x,
+                                  double *y, void *stream);
+
 /* Number of kernels this handle has launched since it was built (build included). */
 long long ccgf_launch_count(const ccgf_handle *h);
 

@@ -43,7 +43,8 @@ class Stats(C.Structure):
 
 
 EXPORTS = ["ccgf_default_options", "ccgf_build_intermediates", "ccgf_dims", "ccgf_sigma_ip", "ccgf_sigma_ea",
-           "ccgf_rhs", "ccgf_left", "ccgf_solve_gf", "ccgf_sigma_profile", "ccgf_sigma_step_name", "ccgf_launch_count", "ccgf_destroy",
+           "ccgf_rhs", "ccgf_left", "ccgf_solve_gf", "ccgf_sigma_profile", "ccgf_sigma_step_name", "ccgf_sigma_ip_noalloc", "ccgf_launch_count",
+           "ccgf_destroy",
            "ccgf_status_string", "ccgf_last_error"]
 
 _lib = None
@@ -77,6 +78,8 @@ def load(path: str | None = None):
     lib.ccgf_sigma_profile.restype = i
     lib.ccgf_sigma_step_name.argtypes = [vp, i, i, i]
     lib.ccgf_sigma_step_name.restype = C.c_char_p
+    lib.ccgf_sigma_ip_noalloc.argtypes = [vp, i, ll, vp, vp, vp]
+    lib.ccgf_sigma_ip_noalloc.restype = i
     lib.ccgf_launch_count.argtypes = [vp]
     lib.ccgf_launch_count.restype = ll
     lib.ccgf_destroy.argtypes = [vp]
@@ -185,6 +188,12 @@ def sigma_ip(h: Handle, kshift, x, y, prec=FP64, stream=None):
 def sigma_ea(h: Handle, kshift, x, y, prec=FP64, stream=None):
     nvec = x.shape[0] if x.ndim == 2 else 1
     return _check(load().ccgf_sigma_ea(h.ptr, kshift, nvec, _ptr(x), _ptr(y), prec, _stream_ptr(stream)))
+
+
+def sigma_ip_noalloc(h: Handle, kshift, x, y, stream=None):
+    """ccgf_sigma_ip_noalloc: FP64 IP sigma using only the library's static device workspace."""
+    nvec = x.shape[0] if x.ndim == 2 else 1
+    return _check(load().ccgf_sigma_ip_noalloc(h.ptr, kshift, nvec, _ptr(x), _ptr(y), _stream_ptr(stream)))
 
 
 def sigma_profile(h: Handle, sector, kshift, x, y, prec=FP64, stream=None, max_steps=64):

@@ -52,6 +52,7 @@ def test_host_side_validation_without_gpu(lib):
     assert lib.ccgf_build_intermediates(ctypes.byref(s), None, None, ctypes.byref(h)) == B.CCGF_ERR_INVALID_ARG
     assert b"kmesh" in lib.ccgf_last_error()
     assert lib.ccgf_sigma_ip(None, 0, 1, None, None, 0, None) == B.CCGF_ERR_INVALID_ARG
+    assert lib.ccgf_sigma_ip_noalloc(None, 0, 1, None, None, None) == B.CCGF_ERR_INVALID_ARG
     assert lib.ccgf_solve_gf(None, 3, 1, None, 0.01, None, None, 0, None, None) == B.CCGF_ERR_INVALID_ARG
     assert lib.ccgf_launch_count(None) == 0
 
