@@ -144,32 +144,36 @@ __global__ void left_kernel(VD D, int sector, int K, int q, double2 *out, i64 ld
 }
 
 // Reduction part of e1 (IP occupied q / EA virtual q): one block per output element.
+//   IP: sum over (kl, kc, l, c, d): nk^2 nocc nvir^2 terms
+//   EA: sum over (kk, kl, k, l, d): nk^2 nocc^2 nvir terms
 __global__ void left_reduce_kernel(VD D, int sector, int K, int q, double2 *out, i64 ld) {
     const int o = D.o, v = D.v, nk = D.nk;
     const int elem = blockIdx.x;   // i (IP) or a (EA)
-    const i64 total = (i64)nk * nk * o * v * v;
+    const i64 total = sector == CCGF_SECTOR_IP ? (i64)nk * nk * o * v * v : (i64)nk * nk * o * o * v;
     double sx = 0, sy = 0;
     for (i64 t = threadIdx.x; t < total; t += blockDim.x) {
-        i64 e = t;
-        int d = e % v; e /= v;
-        int c = e % v; e /= v;
-        int l = e % o; e /= o;
-        int k2 = e % nk;
-        int k1 = (int)(e / nk);
         double2 prod;
         if (sector == CCGF_SECTOR_IP) {
-            // (2t[K,kl,kc][q,l,c,d] - t[K,kl,kd][q,l,d,c]) l2[K,kl,kc][i,l,c,d], kl = k1, kc = k2
-            int kl = k1, kc = k2, kd = kcv(D, K, kc, kl);
+            // (2t[K,kl,kc][q,l,c,d] - t[K,kl,kd][q,l,d,c]) l2[K,kl,kc][i,l,c,d]
+            i64 e = t;
+            int d = e % v; e /= v;
+            int c = e % v; e /= v;
+            int l = e % o; e /= o;
+            int kc = e % nk;
+            int kl = (int)(e / nk);
+            int kd = kcv(D, K, kc, kl);
             double2 tt = ca(cs(D.t2[t2i(D, K, kl, kc, q, l, c, d)], 2.0), cs(D.t2[t2i(D, K, kl, kd, q, l, d, c)], -1.0));
             prod = cm(tt, D.l2[t2i(D, K, kl, kc, elem, l, c, d)]);
         } else {
-            // t2[kk,kl,K][k,l,c,d] (2 l2[kk,kl,K][k,l,a,d] - l2[kl,kk,K][l,k,a,d]); here (k1,k2)=(kk,kl),
-            // l = k index, c = l index, d = d index
-            int kk = k1, kl = k2;
-            int kidx = l, lidx = c;
-            if (lidx >= o) continue;
-            double2 ll = ca(cs(D.l2[t2i(D, kk, kl, K, kidx, lidx, elem, d)], 2.0), cs(D.l2[t2i(D, kl, kk, K, lidx, kidx, elem, d)], -1.0));
-            prod = cm(D.t2[t2i(D, kk, kl, K, kidx, lidx, q - o, d)], ll);
+            // t2[kk,kl,K][k,l,c,d] (2 l2[kk,kl,K][k,l,a,d] - l2[kl,kk,K][l,k,a,d]), c = q - nocc
+            i64 e = t;
+            int d = e % v; e /= v;
+            int l = e % o; e /= o;
+            int k = e % o; e /= o;
+            int kl = e % nk;
+            int kk = (int)(e / nk);
+            double2 ll = ca(cs(D.l2[t2i(D, kk, kl, K, k, l, elem, d)], 2.0), cs(D.l2[t2i(D, kl, kk, K, l, k, elem, d)], -1.0));
+            prod = cm(D.t2[t2i(D, kk, kl, K, k, l, q - o, d)], ll);
         }
         sx += prod.x;
         sy += prod.y;
