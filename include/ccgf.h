@@ -78,6 +78,9 @@ typedef struct {
     int max_refine;           /* cap on FP64 true-residual checks (refinement cycles)      */
     int omega_chunk;          /* frequencies solved together per (sector, K) batch         */
     double device_wait_timeout_ms; /* reserved for bounded device waits                   */
+    int warm_start;           /* 1: initial vectors from the trained warm-start network
+                                 (ccgf_train_warmstart), kept per column only when their true
+                                 residual is below the cold start's |b|                    */
 } ccgf_options;
 
 typedef struct {
@@ -89,11 +92,16 @@ typedef struct {
     double sigma_ms;            /* device time in sigma (CUDA events)                     */
     double total_ms;            /* device time of the whole solve                         */
     long long kernel_launches;  /* kernels launched by the solve                          */
+    long long warm_columns;     /* right-hand sides that started from the network's x0    */
+    long long warm_fallbacks;   /* right-hand sides where the cold start was kept         */
+    double warm_val_loss;       /* ccgf_train_warmstart: validation loss of the network   */
+    double warm_val_loss_baseline; /* ... of the baseline alone (zero correction)         */
 } ccgf_stats;
 
 typedef struct ccgf_handle ccgf_handle;
 
-/* Default options: FP64, tol 1e-10, restart 30, max_iter 2000, max_refine 20, omega_chunk 1. */
+/* Default options: FP64, tol 1e-10, restart 30, max_iter 2000, max_refine 20, omega_chunk 1,
+ * no warm start. */
 void ccgf_default_options(ccgf_options *opt);
 
 /* Build the similarity-transformed Hamiltonian blocks (Eq. 5) for the EOM-CCSD
@@ -134,6 +142,32 @@ ccgf_status ccgf_left(ccgf_handle *h, int sector, int K, int p, double *out, voi
 ccgf_status ccgf_solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omega,
                           double eta, const ccgf_options *opt, double *G_out, int G_on_device,
                           ccgf_stats *stats, void *stream);
+
+/* Learned warm start (no counterpart in the paper's method; it only changes the initial
+ * vectors of the Eq. 6 solves): solves all sectors' right-hand sides at the n_train
+ * training frequencies (ascending, >= 3) with opt (cold start), keeps their solutions in
+ * the handle, then trains the per-element network (14 features -> 256 -> 256 -> 2, tanh,
+ * bfloat16-rounded weights in the forward pass, FP32 accumulation) with Adam for `steps`
+ * steps of rows_per_step random elements of interior training frequencies, each predicted
+ * from its two neighbours. The network predicts a correction to a baseline (the neighbours'
+ * solutions carried to the new frequency along each element's diagonal resolvent); after
+ * training it is kept only if its validation loss beats the baseline's (steps = 0: baseline
+ * only). Later solves with opt->warm_start = 1 use it. final_loss (the kept model's
+ * validation loss) and stats may be NULL. Errors: INVALID_ARG, OOM, CUDA, NAN (diverged). */
+ccgf_status ccgf_train_warmstart(ccgf_handle *h, int sectors, int n_train, const double *omega_train,
+                                 double eta, const ccgf_options *opt, int steps,
+                                 long long rows_per_step, double lr, unsigned seed,
+                                 double *final_loss, ccgf_stats *stats, void *stream);
+
+/* The warm-start network on its own (device pointers, float32): parameters theta =
+ * W1 [F][H], b1 [H], W2 [H][H], b2 [H], W3 [H][2], b3 [2] (ccgf_mlp_param_count(F, H)
+ * floats); X [rows][F]; T, Y [rows][2]. bf16 != 0 rounds W1, W2, W3 to bfloat16 first.
+ * Loss = sum (Y - T)^2 / rows; grad (device, param count floats) is its gradient. */
+long long ccgf_mlp_param_count(int F, int H);
+ccgf_status ccgf_mlp_forward(int F, int H, long long rows, const float *theta, const float *X,
+                             int bf16, float *Y, void *stream);
+ccgf_status ccgf_mlp_loss_grad(int F, int H, long long rows, const float *theta, const float *X,
+                               const float *T, int bf16, double *loss, float *grad, void *stream);
 
 /* Measurement helper (no counterpart in the paper): runs one sigma call like
  * ccgf_sigma_ip / ccgf_sigma_ea (sector = CCGF_SECTOR_IP / EA) with a CUDA event

@@ -29,14 +29,16 @@ class System(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("prec", C.c_int), ("tol", C.c_double), ("restart_m", C.c_int), ("max_iter", C.c_int),
-                ("max_refine", C.c_int), ("omega_chunk", C.c_int), ("device_wait_timeout_ms", C.c_double)]
+                ("max_refine", C.c_int), ("omega_chunk", C.c_int), ("device_wait_timeout_ms", C.c_double),
+                ("warm_start", C.c_int)]
 
 
 class Stats(C.Structure):
     _fields_ = [("rhs_solved", C.c_longlong), ("inner_iterations", C.c_longlong),
                 ("fp64_sigma_calls", C.c_longlong), ("lowp_sigma_calls", C.c_longlong),
                 ("max_rel_residual", C.c_double), ("sigma_ms", C.c_double), ("total_ms", C.c_double),
-                ("kernel_launches", C.c_longlong)]
+                ("kernel_launches", C.c_longlong), ("warm_columns", C.c_longlong), ("warm_fallbacks", C.c_longlong),
+                ("warm_val_loss", C.c_double), ("warm_val_loss_baseline", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -44,7 +46,7 @@ class Stats(C.Structure):
 
 EXPORTS = ["ccgf_default_options", "ccgf_build_intermediates", "ccgf_dims", "ccgf_sigma_ip", "ccgf_sigma_ea",
            "ccgf_rhs", "ccgf_left", "ccgf_solve_gf", "ccgf_sigma_profile", "ccgf_sigma_step_name", "ccgf_sigma_ip_noalloc", "ccgf_launch_count",
-           "ccgf_destroy",
+           "ccgf_train_warmstart", "ccgf_mlp_param_count", "ccgf_mlp_forward", "ccgf_mlp_loss_grad", "ccgf_destroy",
            "ccgf_status_string", "ccgf_last_error"]
 
 _lib = None
@@ -80,6 +82,15 @@ def load(path: str | None = None):
     lib.ccgf_sigma_step_name.restype = C.c_char_p
     lib.ccgf_sigma_ip_noalloc.argtypes = [vp, i, ll, vp, vp, vp]
     lib.ccgf_sigma_ip_noalloc.restype = i
+    lib.ccgf_train_warmstart.argtypes = [vp, i, i, vp, d, C.POINTER(Options), i, ll, d, C.c_uint, C.POINTER(d),
+                                         C.POINTER(Stats), vp]
+    lib.ccgf_train_warmstart.restype = i
+    lib.ccgf_mlp_param_count.argtypes = [i, i]
+    lib.ccgf_mlp_param_count.restype = ll
+    lib.ccgf_mlp_forward.argtypes = [i, i, ll, vp, vp, i, vp, vp]
+    lib.ccgf_mlp_forward.restype = i
+    lib.ccgf_mlp_loss_grad.argtypes = [i, i, ll, vp, vp, vp, i, C.POINTER(d), vp, vp]
+    lib.ccgf_mlp_loss_grad.restype = i
     lib.ccgf_launch_count.argtypes = [vp]
     lib.ccgf_launch_count.restype = ll
     lib.ccgf_destroy.argtypes = [vp]
@@ -194,6 +205,34 @@ def sigma_ip_noalloc(h: Handle, kshift, x, y, stream=None):
     """ccgf_sigma_ip_noalloc: FP64 IP sigma using only the library's static device workspace."""
     nvec = x.shape[0] if x.ndim == 2 else 1
     return _check(load().ccgf_sigma_ip_noalloc(h.ptr, kshift, nvec, _ptr(x), _ptr(y), _stream_ptr(stream)))
+
+
+def train_warmstart(h: Handle, sectors, omega_train, eta, *, options=None, steps=400, rows=65536, lr=2e-3, seed=1,
+                    stream=None):
+    """Solve the training frequencies and train the warm-start network; returns (final loss, stats dict)."""
+    om = np.ascontiguousarray(np.asarray(omega_train, dtype=np.float64))
+    st = Stats()
+    loss = C.c_double()
+    opt = options or default_options()
+    _check(load().ccgf_train_warmstart(h.ptr, sectors, len(om), om.ctypes.data, float(eta), C.byref(opt), steps, rows,
+                                       lr, seed, C.byref(loss), C.byref(st), _stream_ptr(stream)))
+    return loss.value, st.as_dict()
+
+
+def mlp_param_count(F, H):
+    return int(load().ccgf_mlp_param_count(F, H))
+
+
+def mlp_forward(F, H, theta, X, Y, bf16=True, stream=None):
+    return _check(load().ccgf_mlp_forward(F, H, X.shape[0], _ptr(theta), _ptr(X), 1 if bf16 else 0, _ptr(Y),
+                                          _stream_ptr(stream)))
+
+
+def mlp_loss_grad(F, H, theta, X, T, grad, bf16=True, stream=None):
+    loss = C.c_double()
+    _check(load().ccgf_mlp_loss_grad(F, H, X.shape[0], _ptr(theta), _ptr(X), _ptr(T), 1 if bf16 else 0, C.byref(loss),
+                                     _ptr(grad), _stream_ptr(stream)))
+    return loss.value
 
 
 def sigma_profile(h: Handle, sector, kshift, x, y, prec=FP64, stream=None, max_steps=64):

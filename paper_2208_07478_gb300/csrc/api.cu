@@ -18,6 +18,7 @@ __global__ void conj_kernel(const double2 *a, double2 *b, i64 n) {
 
 void destroy(ccgf_handle *h) {
     if (!h) return;
+    warmstart_free(h);
     free_plans(h);
     dfree(h->t1);
     dfree(h->t2);
@@ -50,6 +51,7 @@ void ccgf_default_options(ccgf_options *opt) {
     opt->max_refine = 20;
     opt->omega_chunk = 1;
     opt->device_wait_timeout_ms = 1000.0;
+    opt->warm_start = 0;
 }
 
 const char *ccgf_status_string(ccgf_status s) {
@@ -220,6 +222,35 @@ const char *ccgf_sigma_step_name(const ccgf_handle *h, int sector, int kshift, i
 }
 
 long long ccgf_launch_count(const ccgf_handle *h) { return h ? h->launches : 0; }
+
+ccgf_status ccgf_train_warmstart(ccgf_handle *h, int sectors, int n_train, const double *omega_train, double eta,
+                                 const ccgf_options *opt, int steps, long long rows_per_step, double lr, unsigned seed,
+                                 double *final_loss, ccgf_stats *stats, void *stream) {
+    if (!h || !omega_train || n_train < 3 || sectors < 1 || sectors > 3 || steps < 0 || rows_per_step < 64 ||
+        rows_per_step > (1LL << 22) || !(lr > 0) || !(eta > 0)) {
+        set_last_error("invalid warm-start training arguments (n_train >= 3, steps >= 0, 64 <= rows <= 4M, lr, eta > 0)");
+        return CCGF_ERR_INVALID_ARG;
+    }
+    for (int i = 1; i < n_train; ++i)
+        if (!(omega_train[i] > omega_train[i - 1])) { set_last_error("training frequencies must increase"); return CCGF_ERR_INVALID_ARG; }
+    cudaStream_t st = (cudaStream_t)stream;
+    ccgf_options o;
+    if (opt) o = *opt;
+    else ccgf_default_options(&o);
+    o.warm_start = 0;
+    CCGF_TRY(warmstart_begin_capture(h, omega_train, n_train, eta));
+    const i64 Gn = (i64)h->nk * n_train * h->n * h->n;
+    DBuf<double2> G;
+    CCGF_TRY(dalloc(G, Gn));
+    h->ws_capturing = true;
+    ccgf_status s = solve_gf(h, sectors, n_train, omega_train, eta, &o, (double *)G.p, 1, stats, st);
+    h->ws_capturing = false;
+    dfree(G);
+    if (s != CCGF_OK && s != CCGF_NOT_CONVERGED) return s;
+    s = warmstart_train(h, sectors, steps, rows_per_step, lr, seed, final_loss, st);
+    if (s == CCGF_OK && stats) warmstart_losses(h, &stats->warm_val_loss, &stats->warm_val_loss_baseline);
+    return s;
+}
 
 void ccgf_destroy(ccgf_handle *h) { destroy(h); }
 

@@ -119,6 +119,7 @@ enum {
     NBUF
 };
 
+struct WarmStart;
 struct ccgf_handle {
     int device;
     KMeshH km;
@@ -139,6 +140,9 @@ struct ccgf_handle {
     std::vector<SigmaPlan *> plans;
     int plan_nv = 0;
     i64 launches = 0;
+    // learned warm start (mlp.cu); capture of training solutions while ws_capturing
+    WarmStart *ws = nullptr;
+    bool ws_capturing = false;
     // optional per-step timing of one sigma call (ccgf_sigma_profile)
     cudaEvent_t *prof_events = nullptr;
     int prof_max = 0, prof_count = 0;
@@ -162,7 +166,19 @@ ccgf_status make_left(ccgf_handle *h, int sector, int K, int p, double2 *out, i6
 // transposes between [nvec][D] (ABI) and [D][nv] (internal)
 void launch_transpose_in(const double2 *x, double2 *xt, i64 D, int nvec, int nv, cudaStream_t st);
 void launch_transpose_out(const double2 *yt, double2 *y, i64 D, int nvec, int nv, cudaStream_t st);
+// mlp.cu
+ccgf_status warmstart_begin_capture(ccgf_handle *h, const double *omega, int n, double eta);
+ccgf_status warmstart_capture(ccgf_handle *h, int sector, int K, const double2 *X, i64 D, int nw, int w0, const double *bnorm2_h,
+                              cudaStream_t st);
+// x0 of the network into X; when the learned correction is in use, the baseline alone into Xbase
+ccgf_status warmstart_infer(ccgf_handle *h, int sector, int K, const double *om, int nw, const double *dvec, double2 *X,
+                            double2 *Xbase, bool *used, bool *net, cudaStream_t st);
+ccgf_status warmstart_train(ccgf_handle *h, int sectors, int steps, i64 rows, double lr, unsigned seed, double *final_loss,
+                            cudaStream_t st);
+void warmstart_free(ccgf_handle *h);
+void warmstart_losses(const ccgf_handle *h, double *val_net, double *val_base);
 // solve.cu
+ccgf_status diag_estimate_device(ccgf_handle *h, int sector, int K, double *d, cudaStream_t st);
 ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omega, double eta,
                      const ccgf_options *opt, double *G_out, int G_on_device, ccgf_stats *stats,
                      cudaStream_t st);

@@ -2,6 +2,7 @@
 // permute-add, layout transposes, plus small shared helpers of the library.
 #include "ccgf_internal.h"
 #include <mutex>
+#include <cmath>
 
 static thread_local std::string g_last_error;
 void set_last_error(const std::string &msg) { g_last_error = msg; }
@@ -53,17 +54,18 @@ template <typename T, typename S> __device__ __forceinline__ void cfma(T &acc, c
 }
 
 // ----------------------------------------------------------------------------- batched GEMM
-// 64x64 output tile per CTA, 256 threads, 4x4 complex outputs per thread (rows ty+16i,
-// columns tx+16j), K staged through shared memory 16 at a time. Loads pick the
-// coalesced mapping from whichever operand stride is 1. Out-of-range rows/columns
-// of a tile are zero-filled on load and masked on store.
-template <typename R>
+// (16 TM) x (16 TN) output tile per CTA, 256 threads, TM x TN complex outputs per thread (rows
+// ty + 16 i, columns tx + 16 j), K staged through shared memory 16 at a time. Loads pick the
+// coalesced mapping from whichever operand stride is 1. Out-of-range rows / columns of a tile
+// are zero-filled on load and masked on store. The launcher picks (TM, TN) per GEMM to keep
+// tile padding small (e.g. 88 rows -> 2 x 48 instead of 2 x 64).
+template <typename R, int TM, int TN>
 __global__ void __launch_bounds__(256) zgemm_kernel(GemmDesc d, const typename cvec<R>::T *__restrict__ A,
                                                     const typename cvec<R>::T *__restrict__ B,
                                                     typename cvec<R>::T *__restrict__ C, int ksplit, int kchunk,
                                                     typename cvec<R>::T *__restrict__ work) {
     typedef typename cvec<R>::T T;
-    constexpr int BM = 64, BN = 64, BK = 16;
+    constexpr int BM = 16 * TM, BN = 16 * TN, BK = 16;
     __shared__ T As[BK][BM];
     __shared__ T Bs[BK][BN];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -74,41 +76,41 @@ __global__ void __launch_bounds__(256) zgemm_kernel(GemmDesc d, const typename c
     for (int bz = blockIdx.z; bz < d.batch * ksplit; bz += gridDim.z) {
         const int b = bz / ksplit, ks = bz % ksplit;
         const int kbeg = ks * kchunk, kend = min(d.K, kbeg + kchunk);
-        T acc[4][4];
+        T acc[TM][TN];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < TM; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = cz<T>();
+            for (int j = 0; j < TN; ++j) acc[i][j] = cz<T>();
         for (int r = 0; r < d.nred; ++r) {
             const T *Ab = A + d.offA[(i64)b * d.nred + r];
             const T *Bb = B + d.offB[(i64)b * d.nred + r];
             for (int k0 = kbeg; k0 < kend; k0 += BK) {
 #pragma unroll
-                for (int s = 0; s < 4; ++s) {
+                for (int s = 0; s < TM; ++s) {
                     int l = tid + 256 * s, i, kk;
-                    if (d.csA == 1) { kk = l & 15; i = l >> 4; } else { i = l & 63; kk = l >> 6; }
+                    if (d.csA == 1) { kk = l & 15; i = l >> 4; } else { i = l % BM; kk = l / BM; }
                     int m = m0 + i, k = k0 + kk;
                     As[kk][i] = (m < d.M && k < kend) ? Ab[(i64)m * d.rsA + (i64)k * d.csA] : cz<T>();
                 }
 #pragma unroll
-                for (int s = 0; s < 4; ++s) {
+                for (int s = 0; s < TN; ++s) {
                     int l = tid + 256 * s, nn, kk;
-                    if (d.csB == 1) { nn = l & 63; kk = l >> 6; } else { kk = l & 15; nn = l >> 4; }
+                    if (d.csB == 1) { nn = l % BN; kk = l / BN; } else { kk = l & 15; nn = l >> 4; }
                     int n = n0 + nn, k = k0 + kk;
                     Bs[kk][nn] = (n < d.N && k < kend) ? Bb[(i64)k * d.rsB + (i64)n * d.csB] : cz<T>();
                 }
                 __syncthreads();
 #pragma unroll
                 for (int kk = 0; kk < BK; ++kk) {
-                    T a[4], bb[4];
+                    T a[TM], bb[TN];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+                    for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+                    for (int j = 0; j < TN; ++j) bb[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
+                    for (int i = 0; i < TM; ++i)
 #pragma unroll
-                        for (int j = 0; j < 4; ++j) cfma<T, R>(acc[i][j], a[i], bb[j]);
+                        for (int j = 0; j < TN; ++j) cfma<T, R>(acc[i][j], a[i], bb[j]);
                 }
                 __syncthreads();
             }
@@ -117,11 +119,11 @@ __global__ void __launch_bounds__(256) zgemm_kernel(GemmDesc d, const typename c
             // raw partial sums to work[b][ks][M][N]; zgemm_splitk_reduce applies alpha and beta
             T *Wb = work + ((i64)b * ksplit + ks) * (i64)d.M * d.N;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
+            for (int i = 0; i < TM; ++i) {
                 int m = m0 + ty + 16 * i;
                 if (m >= d.M) continue;
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
+                for (int j = 0; j < TN; ++j) {
                     int n = n0 + tx + 16 * j;
                     if (n < d.N) Wb[(i64)m * d.N + n] = acc[i][j];
                 }
@@ -130,11 +132,11 @@ __global__ void __launch_bounds__(256) zgemm_kernel(GemmDesc d, const typename c
         }
         T *Cb = C + d.offC[b];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < TM; ++i) {
             int m = m0 + ty + 16 * i;
             if (m >= d.M) continue;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < TN; ++j) {
                 int n = n0 + tx + 16 * j;
                 if (n >= d.N) continue;
                 T *c = Cb + (i64)m * d.rsC + (i64)n * d.csC;
@@ -181,18 +183,53 @@ __global__ void zgemm_splitk_reduce(GemmDesc d, int ksplit, const typename cvec<
     }
 }
 
+// Per-thread tile shapes available to the launcher (rows x columns of complex outputs).
+struct TileShape {
+    int tm, tn;
+};
+static const TileShape kShapes[] = {{4, 4}, {3, 4}, {2, 4}, {4, 3}, {4, 2}, {4, 7}, {3, 7}, {2, 7}};
+
+// Shape with the least padded work divided by the wave efficiency (whole waves of one CTA per
+// SM), with a slight preference for larger tiles (higher register reuse).
+static TileShape pick_shape(const GemmDesc &d) {
+    TileShape best = kShapes[0];
+    double best_cost = 1e300;
+    for (const TileShape &s : kShapes) {
+        const i64 bm = 16 * s.tm, bn = 16 * s.tn;
+        const double padded = (double)ceil_div(d.M, bm) * bm * (double)ceil_div(d.N, bn) * bn;
+        const double ctas = (double)ceil_div(d.M, bm) * ceil_div(d.N, bn) * d.batch;
+        const double waves = ctas / 152.0;
+        const double wave_eff = waves >= 1.0 ? waves / std::ceil(waves) : waves;
+        const double cost = padded / wave_eff * (1.0 + 0.02 * (16.0 / (s.tm * s.tn)));
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = s;
+        }
+    }
+    return best;
+}
+
 int zgemm_ksplit(const GemmDesc &d) {
     // Enough CTAs to cover the SMs twice; every split keeps at least 8 k-tiles of work.
-    const i64 tiles = ceil_div(d.M, 64) * ceil_div(d.N, 64) * (i64)d.batch;
+    const TileShape s = pick_shape(d);
+    const i64 tiles = ceil_div(d.M, 16 * s.tm) * ceil_div(d.N, 16 * s.tn) * (i64)d.batch;
     if (tiles >= 304 || d.nred != 1) return 1;
-    i64 s = ceil_div(304, tiles);
-    i64 smax = d.K / 128;
-    if (s > smax) s = smax;
-    return (int)(s < 1 ? 1 : s);
+    i64 k = ceil_div(304, tiles);
+    i64 kmax = d.K / 128;
+    if (k > kmax) k = kmax;
+    return (int)(k < 1 ? 1 : k);
 }
 i64 zgemm_workspace_elems(const GemmDesc &d) {
     int s = zgemm_ksplit(d);
     return s > 1 ? (i64)s * d.M * d.N * d.batch : 0;
+}
+
+template <typename R, int TM, int TN>
+static void launch_shape(const GemmDesc &d, const typename cvec<R>::T *A, const typename cvec<R>::T *B, typename cvec<R>::T *C,
+                         cudaStream_t st, int ks, int kchunk, typename cvec<R>::T *work) {
+    i64 z = (i64)d.batch * ks;
+    dim3 grid((unsigned)ceil_div(d.N, 16 * TN), (unsigned)ceil_div(d.M, 16 * TM), (unsigned)(z < 65535 ? z : 65535));
+    zgemm_kernel<R, TM, TN><<<grid, 256, 0, st>>>(d, A, B, C, ks, kchunk, work);
 }
 
 template <typename R>
@@ -206,9 +243,15 @@ int launch_zgemm(const GemmDesc &d, const typename cvec<R>::T *A, const typename
         kchunk = (int)(ceil_div(ceil_div(d.K, ks), 16) * 16);
         ks = (int)ceil_div(d.K, kchunk);
     }
-    i64 z = (i64)d.batch * ks;
-    dim3 grid((unsigned)ceil_div(d.N, 64), (unsigned)ceil_div(d.M, 64), (unsigned)(z < 65535 ? z : 65535));
-    zgemm_kernel<R><<<grid, 256, 0, st>>>(d, A, B, C, ks, kchunk, work);
+    const TileShape s = pick_shape(d);
+    if (s.tm == 4 && s.tn == 4) launch_shape<R, 4, 4>(d, A, B, C, st, ks, kchunk, work);
+    else if (s.tm == 3 && s.tn == 4) launch_shape<R, 3, 4>(d, A, B, C, st, ks, kchunk, work);
+    else if (s.tm == 2 && s.tn == 4) launch_shape<R, 2, 4>(d, A, B, C, st, ks, kchunk, work);
+    else if (s.tm == 4 && s.tn == 3) launch_shape<R, 4, 3>(d, A, B, C, st, ks, kchunk, work);
+    else if (s.tm == 4 && s.tn == 2) launch_shape<R, 4, 2>(d, A, B, C, st, ks, kchunk, work);
+    else if (s.tm == 4 && s.tn == 7) launch_shape<R, 4, 7>(d, A, B, C, st, ks, kchunk, work);
+    else if (s.tm == 3 && s.tn == 7) launch_shape<R, 3, 7>(d, A, B, C, st, ks, kchunk, work);
+    else launch_shape<R, 2, 7>(d, A, B, C, st, ks, kchunk, work);
     if (ks > 1) {
         i64 n = (i64)d.M * d.N * d.batch;
         i64 g = ceil_div(n, 256);

@@ -297,7 +297,31 @@ inline unsigned g1(i64 n) {
     return (unsigned)std::max<i64>(1, std::min<i64>(g, 152 * 16));
 }
 
+// per column: mode 0 -> x0 = 0, r = b (cold); 1 -> keep (X, R); 2 -> (Xb, Rb)
+__global__ void select_kernel(const int *mode, double2 *X, double2 *R, const double2 *Xb, const double2 *Rb, const double2 *B,
+                              i64 D, int nv) {
+    for (i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x; t < D * nv; t += (i64)gridDim.x * blockDim.x) {
+        int md = mode[t % nv];
+        if (md == 0) {
+            X[t] = make_double2(0, 0);
+            R[t] = B[t];
+        } else if (md == 2) {
+            X[t] = Xb[t];
+            R[t] = Rb[t];
+        }
+    }
+}
+
 }  // namespace
+
+ccgf_status diag_estimate_device(ccgf_handle *h, int sector, int K, double *d, cudaStream_t st) {
+    const i64 D = sector == CCGF_SECTOR_IP ? h->dim_ip : h->dim_ea;
+    diag_kernel<<<g1(D), 256, 0, st>>>(sector, K, h->nk, h->o, h->v, h->kadd_d.p, h->ksub_d.p, h->W[BUF_FOO].p,
+                                       h->W[BUF_FVV].p, d, D);
+    h->launches++;
+    CCGF_CUDA_TRY(cudaGetLastError());
+    return CCGF_OK;
+}
 
 ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omega, double eta, const ccgf_options *opt,
                      double *G_out, int G_on_device, ccgf_stats *stats, cudaStream_t st) {
@@ -402,6 +426,42 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                 std::vector<double> tg(nv);
                 for (int c = 0; c < nv; ++c) tg[c] = tol * std::sqrt(b2[c]);
                 CCGF_CUDA_TRY(cudaMemcpyAsync(target.p, tg.data(), sizeof(double) * nv, cudaMemcpyHostToDevice, st));
+                if (opt->warm_start) {
+                    // learned initial vectors: per column keep the candidate (network, baseline, cold) with the
+                    // smallest true residual; the cold start's residual is |b|
+                    bool used = false, net = false;
+                    CCGF_TRY(warmstart_infer(h, sector, K, omega + w0, nw, dvec.p, X.p, U.p, &used, &net, st));
+                    if (used) {
+                        auto resid2 = [&](const double2 *x, double2 *r, std::vector<double> &out) -> ccgf_status {
+                            CCGF_TRY(sigma_apply(h, sector, K, nv, x, AU.p, opt->prec, st));
+                            if (opt->prec == CCGF_FP64) S.fp64_sigma_calls++; else S.lowp_sigma_calls++;
+                            residual_kernel<<<g1(Dn), 256, 0, st>>>(Sh, B.p, x, AU.p, r, D, nv);
+                            h->launches++;
+                            CCGF_CUDA_TRY(cudaMemsetAsync(beta2.p, 0, sizeof(double) * nv, st));
+                            colnorm2_kernel<<<rgrid, dim3(32, 8), 0, st>>>(r, beta2.p, D, nv, rpb);
+                            h->launches++;
+                            out.resize(nv);
+                            CCGF_CUDA_TRY(cudaMemcpyAsync(out.data(), beta2.p, sizeof(double) * nv, cudaMemcpyDeviceToHost, st));
+                            CCGF_CUDA_TRY(cudaStreamSynchronize(st));
+                            return CCGF_OK;
+                        };
+                        std::vector<double> rn, rb;
+                        CCGF_TRY(resid2(X.p, R.p, rn));
+                        if (net) CCGF_TRY(resid2(U.p, V.p, rb));     // baseline candidate (V slot 0 is free here)
+                        std::vector<int> mode(nv);                     // 0 cold, 1 network / baseline-only, 2 baseline
+                        for (int c = 0; c < nv; ++c) {
+                            double best = b2[c];
+                            mode[c] = 0;
+                            if (rn[c] < best) { best = rn[c]; mode[c] = 1; }
+                            if (net && rb[c] < best) { best = rb[c]; mode[c] = 2; }
+                            S.warm_columns += mode[c] ? 1 : 0;
+                            S.warm_fallbacks += mode[c] ? 0 : 1;
+                        }
+                        CCGF_CUDA_TRY(cudaMemcpyAsync(active.p, mode.data(), sizeof(int) * nv, cudaMemcpyHostToDevice, st));
+                        select_kernel<<<g1(Dn), 256, 0, st>>>(active.p, X.p, R.p, U.p, V.p, B.p, D, nv);
+                        h->launches++;
+                    }
+                }
                 i64 it_total = 0;
                 int cycles = 0;
                 bool converged = false;
@@ -499,6 +559,7 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                     residual_kernel<<<g1(Dn), 256, 0, st>>>(Sh, B.p, X.p, AU.p, R.p, D, nv);
                     h->launches++;
                 }
+                if (h->ws_capturing) CCGF_TRY(warmstart_capture(h, sector, K, X.p, D, nw, w0, b2.data(), st));
                 S.inner_iterations += it_total;
                 S.rhs_solved += nv;
                 S.max_rel_residual = std::max(S.max_rel_residual, maxres);

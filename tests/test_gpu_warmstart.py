@@ -1,0 +1,80 @@
+"""Learned warm start on the GPU: the network kernels against the CPU oracle, training on
+solved frequencies, and what it gains on held-out frequencies (without changing G)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2208_07478_gb300 import binding as B
+from paper_2208_07478_gb300.synth import make_system
+from oracle import mlp
+
+
+@pytest.mark.parametrize("bf16,rtol", [(True, 2e-3), (False, 2e-5)])
+def test_network_loss_and_gradient_match_oracle(bf16, rtol):
+    F, H, rows = 12, 256, 777
+    rng = np.random.default_rng(4)
+    theta = mlp.init_params(F, H, 2) + 0.01 * rng.normal(size=mlp.n_params(F, H))
+    theta32 = theta.astype(np.float32)
+    X = rng.normal(size=(rows, F)).astype(np.float32)
+    T = (0.3 * rng.normal(size=(rows, 2))).astype(np.float32)
+    assert B.mlp_param_count(F, H) == theta.size
+    dth, dX, dT = (torch.from_numpy(a).cuda() for a in (theta32, X, T))
+    grad = torch.zeros_like(dth)
+    loss = B.mlp_loss_grad(F, H, dth, dX, dT, grad, bf16=bf16)
+    ref_loss, ref_g = mlp.loss_and_grad(theta32.astype(np.float64), F, H, X.astype(np.float64),
+                                        T.astype(np.float64), bf16=bf16)
+    assert abs(loss - ref_loss) <= rtol * abs(ref_loss)
+    g = grad.cpu().numpy().astype(np.float64)
+    # per parameter block, relative to the block's largest gradient
+    off = 0
+    for shp in mlp.shapes(F, H):
+        n = int(np.prod(shp))
+        blk, rblk = g[off:off + n], ref_g[off:off + n]
+        assert np.abs(blk - rblk).max() <= rtol * max(np.abs(rblk).max(), 1e-12), shp
+        off += n
+    Y = torch.zeros((rows, 2), dtype=torch.float32, device="cuda")
+    B.mlp_forward(F, H, dth, dX, Y, bf16=bf16)
+    yref, _ = mlp.forward(theta32.astype(np.float64), F, H, X.astype(np.float64), bf16=bf16)
+    assert np.abs(Y.cpu().numpy() - yref).max() <= rtol * np.abs(yref).max()
+
+
+def _held_out(steps):
+    s = make_system((2, 1, 1), 2, 6, 8, seed=31, L_sigma=0.08, t1_sigma=0.02, nomega=0, eta=0.02)
+    h = B.build_intermediates(s.kmesh, s.nocc, s.nvir, s.naux, s.mo_energy, s.L, s.t1, s.t2)
+    train = np.linspace(-0.7, 0.7, 15)
+    held = 0.5 * (train[1:] + train[:-1])
+    opt = B.default_options(tol=1e-10, restart_m=40, max_iter=4000)
+    loss, tstats = B.train_warmstart(h, B.BOTH, train, s.eta, options=opt, steps=steps, rows=32768, lr=3e-4, seed=3)
+    Gc = np.zeros((s.nk, len(held), s.nmo, s.nmo), dtype=np.complex128)
+    Gw = np.zeros_like(Gc)
+    st_c, cold = B.solve_gf(h, B.BOTH, held, s.eta, Gc, options=opt)
+    optw = B.default_options(tol=1e-10, restart_m=40, max_iter=4000, warm_start=1)
+    st_w, warm = B.solve_gf(h, B.BOTH, held, s.eta, Gw, options=optw)
+    h.close()
+    print(f"steps {steps}: validation loss network {tstats['warm_val_loss']:.3e}, baseline "
+          f"{tstats['warm_val_loss_baseline']:.3e}; held-out iterations cold {cold['inner_iterations']}, warm "
+          f"{warm['inner_iterations']}; warm columns {warm['warm_columns']}, fallbacks {warm['warm_fallbacks']}")
+    assert st_c == st_w == B.CCGF_OK
+    # the warm start only changes the initial vectors: G agrees within the solver tolerance
+    assert np.abs(Gw - Gc).max() <= 1e-7 * max(1.0, np.abs(Gc).max())
+    assert warm["warm_columns"] + warm["warm_fallbacks"] == warm["rhs_solved"]
+    return cold, warm, loss, tstats
+
+
+def test_baseline_warm_start_gain():
+    """Untrained (zero) correction: the neighbours carried along the diagonal resolvent."""
+    cold, warm, loss, t = _held_out(0)
+    assert warm["warm_columns"] > 0
+    assert warm["inner_iterations"] <= cold["inner_iterations"]
+
+
+def test_trained_network_gain():
+    """Trained network: kept only if it beats the baseline on validation rows; never worse than cold."""
+    cold, warm, loss, t = _held_out(400)
+    assert np.isfinite(loss) and loss <= t["warm_val_loss_baseline"] + 1e-15
+    assert warm["inner_iterations"] <= cold["inner_iterations"]
