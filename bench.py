@@ -10,9 +10,10 @@ successive points of the frequency grid. The timed region also holds one build
 of the similarity-transformed Hamiltonian blocks from device-resident inputs,
 amortised over the K steps.
 
-`value` is the plain FP64 form (every step in FP64). The chosen form (FP32
-sigma inside FP64 refinement, same FP64-verified residual target) is reported
-beside it with its ratio to the plain form.
+`value` is the plain FP64 form (every step in FP64). The chosen form (inner
+sigma on the tensor cores with 3xTF32 operands, inside FP64 refinement, same
+FP64-verified residual target) is reported beside it with its ratio to the
+plain form.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
 
@@ -39,6 +40,17 @@ TOL = 1e-6
 # FP64 SIMT peak: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (the nominal 1.25 TFLOP/s of the part)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# dense TF32 tensor peak: the measured bf16 GEMM burst figure x the nominal TF32/BF16 ratio (1.1/2.25);
+# the 3xTF32 split issues three real MMAs on the 2x2 real embedding of every complex multiply-add
+# (24 real flop per 8 algorithmic flop), so its ceiling in algorithmic flop/s is a third of that
+TF32_NOMINAL_RATIO = 1.1 / 2.25
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
 
 
 def parse():
@@ -49,6 +61,8 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-chosen", action="store_true", help="skip the chosen-form measurement")
+    ap.add_argument("--chosen-prec", default="tf32x3", choices=["tf32x3", "fp32"],
+                    help="inner sigma of the chosen form: tensor cores (3xTF32) or FP32 SIMT")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -246,7 +260,7 @@ def gpu_arm(args):
                       "naux": s.naux, "eta": s.eta, "omega_grid": [float(s.omega[0]), float(s.omega[-1]), nomega],
                       "omega_per_step": 1, "sectors": "ip+ea", "tol": TOL, "form": "plain fp64",
                       "timed": "1 intermediate build + K frequency steps",
-                      "l2": "inputs larger than L2 (W_vvvv 1.9 GB, Krylov basis ~1 GB)",
+                      "l2": "inputs larger than L2 (ladder blocks W+/W- 0.97 GB, Krylov basis ~1 GB)",
                       "parallelism": f"replicas x{world} (frequency points sharded)"},
            "roofline": roof,
            "sigma": {"precision": "fp64", "sector": "ea", "nvec": N, "ms": round(sig_ms, 3),
@@ -258,25 +272,41 @@ def gpu_arm(args):
                       "max_rel_residual": max(float(x["max_rel_residual"]) for x in st64)}}
 
     if not args.no_chosen:
-        ms32, st32, h32 = timed(B.FP32, 0)
+        cprec = B.TF32X3 if args.chosen_prec == "tf32x3" else B.FP32
+        ms32, st32, h32 = timed(cprec, 0)
         ms32 = max_over_ranks(pg, ms32, dev)
         v32 = world * args.steps * elems_per_step / (ms32 / 1e3)
         D = h32.dims()["dim_ea"]
         x = torch.randn((N, D), dtype=torch.complex128, device=dev)
         y = torch.empty_like(x)
-        B.sigma_profile(h32, B.EA, 0, x, y, prec=B.FP32, stream=stream)
-        prof32 = B.sigma_profile(h32, B.EA, 0, x, y, prec=B.FP32, stream=stream)
+        B.sigma_profile(h32, B.EA, 0, x, y, prec=cprec, stream=stream)
+        prof32 = B.sigma_profile(h32, B.EA, 0, x, y, prec=cprec, stream=stream)
         s32_ms = sum(p[1] for p in prof32)
         s32_fl = sum(p[2] for p in prof32)
+        top32 = max(prof32, key=lambda p: p[1])
         h32.close()
-        out["chosen_form"] = {"form": "FP32 sigma inside FP64 refinement (FP64 Krylov basis, FP64 true residual)",
-                              "value": round(v32, 3), "unit": "G elements/s", "ms_per_step": round(ms32 / args.steps, 3),
-                              "ratio_vs_plain_fp64": round(v32 / value, 3),
-                              "max_rel_residual": max(float(x["max_rel_residual"]) for x in st32),
-                              "fp64_sigma_calls": sum(int(x["fp64_sigma_calls"]) for x in st32),
-                              "lowp_sigma_calls": sum(int(x["lowp_sigma_calls"]) for x in st32),
-                              "sigma_fp32_tflops": round(s32_fl / (s32_ms / 1e3) / 1e12, 3),
-                              "sigma_fp32_frac_of_fp32_peak": round(s32_fl / (s32_ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS, 4)}
+        cf = {"value": round(v32, 3), "unit": "G elements/s", "ms_per_step": round(ms32 / args.steps, 3),
+              "ratio_vs_plain_fp64": round(v32 / value, 3),
+              "max_rel_residual": max(float(x["max_rel_residual"]) for x in st32),
+              "fp64_sigma_calls": sum(int(x["fp64_sigma_calls"]) for x in st32),
+              "lowp_sigma_calls": sum(int(x["lowp_sigma_calls"]) for x in st32),
+              "sigma_tflops": round(s32_fl / (s32_ms / 1e3) / 1e12, 3), "sigma_ms": round(s32_ms, 3)}
+        if cprec == B.TF32X3:
+            bf16 = measured_peaks().get("bf16_tflops")
+            peak = bf16 * TF32_NOMINAL_RATIO / 3 if bf16 else 1900.0 * TF32_NOMINAL_RATIO / 3
+            basis = ("measured bf16 burst %.0f TFLOP/s x nominal TF32/BF16 1.1/2.25 / 3 MMAs per product (%s)"
+                     % (bf16 or 1900.0, "of measured" if bf16 else "of fallback"))
+            ach = top32[2] / (top32[1] / 1e3) / 1e12
+            cf["form"] = ("tensor-core sigma (tcgen05 kind::tf32, operands split hi+lo, 3 MMAs, FP32 accumulate) "
+                          "inside FP64 refinement (FP64 Krylov basis, FP64 true residual)")
+            cf["roofline"] = {"bound": "tensor", "kernel": f"tc_zgemm_kernel ({top32[0]})", "achieved": round(ach, 3),
+                              "peak": round(peak, 1), "unit": "TFLOP/s", "frac": round(ach / peak, 4),
+                              "launch_ms": round(top32[1], 4), "algorithmic_flops_per_launch": top32[2],
+                              "peak_basis": basis}
+        else:
+            cf["form"] = "FP32 SIMT sigma inside FP64 refinement (FP64 Krylov basis, FP64 true residual)"
+            cf["sigma_frac_of_fp32_peak"] = round(s32_fl / (s32_ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS, 4)
+        out["chosen_form"] = cf
 
     if not args.no_e2e:
         # end to end through the public API with host buffers: H2D of the inputs from pinned memory,

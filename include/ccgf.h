@@ -48,7 +48,12 @@ typedef enum {
 
 typedef enum {
     CCGF_FP64 = 0,       /* plain form: every step in FP64 */
-    CCGF_FP32 = 1        /* sigma contractions in FP32 (FP32 accumulate) inside FP64 refinement */
+    CCGF_FP32 = 1,       /* sigma contractions in FP32 (FP32 accumulate) inside FP64 refinement */
+    CCGF_TF32X3 = 2      /* sigma contractions on the tensor cores (tcgen05): each FP32 operand split
+                            into two TF32 parts, three products (hi*hi + hi*lo + lo*hi) accumulated
+                            in FP32, inside FP64 refinement; contractions too small for a 128-row
+                            tile run as in CCGF_FP32. A tensor-core wait that runs past its 2 s
+                            limit makes the call return CCGF_ERR_TIMEOUT. */
 } ccgf_precision;
 
 typedef enum { CCGF_SECTOR_IP = 1, CCGF_SECTOR_EA = 2, CCGF_SECTOR_BOTH = 3 } ccgf_sector;

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libccgf.so")
 
 CCGF_OK, CCGF_NOT_CONVERGED = 0, 1
 CCGF_ERR_INVALID_ARG, CCGF_ERR_OOM, CCGF_ERR_CUDA, CCGF_ERR_NAN, CCGF_ERR_TIMEOUT = -1, -2, -3, -4, -5
-FP64, FP32 = 0, 1
+FP64, FP32, TF32X3 = 0, 1, 2
 IP, EA, BOTH = 1, 2, 3
 
 

@@ -28,6 +28,9 @@ void destroy(ccgf_handle *h) {
     dfree(h->eps);
     dfree(h->kadd_d);
     dfree(h->ksub_d);
+    dfree(h->lad_reps);
+    dfree(h->lad_npl);
+    dfree(h->lad_nmi);
     for (int b = 0; b < NBUF; ++b) {
         dfree(h->W[b]);
         dfree(h->Wf[b]);
@@ -35,6 +38,7 @@ void destroy(ccgf_handle *h) {
     dfree(h->scratch);
     dfree(h->scratch_f);
     dfree(h->yf);
+    dfree(h->tc_err);
     delete h;
 }
 
@@ -134,7 +138,7 @@ static ccgf_status sigma_abi(ccgf_handle *h, int sector, int kshift, long long n
     if (!h || !x || !y) { set_last_error("NULL handle or vector"); return CCGF_ERR_INVALID_ARG; }
     if (kshift < 0 || kshift >= h->nk) { set_last_error("kshift out of range"); return CCGF_ERR_INVALID_ARG; }
     if (nvec < 1 || nvec > 65536) { set_last_error("nvec must be in [1, 65536]"); return CCGF_ERR_INVALID_ARG; }
-    if (prec != CCGF_FP64 && prec != CCGF_FP32) { set_last_error("unknown precision"); return CCGF_ERR_INVALID_ARG; }
+    if (prec != CCGF_FP64 && prec != CCGF_FP32 && prec != CCGF_TF32X3) { set_last_error("unknown precision"); return CCGF_ERR_INVALID_ARG; }
     cudaStream_t st = (cudaStream_t)stream;
     const i64 D = sector == CCGF_SECTOR_IP ? h->dim_ip : h->dim_ea;
     const int nv = (int)nvec;
@@ -150,6 +154,7 @@ static ccgf_status sigma_abi(ccgf_handle *h, int sector, int kshift, long long n
     dfree(yt);
     if (s != CCGF_OK) return s;
     if (e != cudaSuccess) { set_last_error(cudaGetErrorString(e)); return CCGF_ERR_CUDA; }
+    if (prec == CCGF_TF32X3) return tc_error_check(h, st);
     return CCGF_OK;
 }
 
@@ -187,7 +192,7 @@ ccgf_status ccgf_solve_gf(ccgf_handle *h, int sectors, int nomega, const double 
         set_last_error("invalid options (tol > 0, restart_m >= 2, max_iter >= 1, max_refine >= 1, omega_chunk >= 1)");
         return CCGF_ERR_INVALID_ARG;
     }
-    if (o.prec != CCGF_FP64 && o.prec != CCGF_FP32) { set_last_error("unknown precision"); return CCGF_ERR_INVALID_ARG; }
+    if (o.prec != CCGF_FP64 && o.prec != CCGF_FP32 && o.prec != CCGF_TF32X3) { set_last_error("unknown precision"); return CCGF_ERR_INVALID_ARG; }
     return solve_gf(h, sectors, nomega, omega, eta, &o, G_out, G_on_device, stats, (cudaStream_t)stream);
 }
 

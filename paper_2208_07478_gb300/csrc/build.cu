@@ -8,6 +8,8 @@
 // straight into the GEMM-ready layout the sigma plans read.
 #include "ccgf_internal.h"
 #include <cmath>
+#include <algorithm>
+#include <vector>
 
 namespace {
 
@@ -464,6 +466,44 @@ __global__ void uooov_kernel(Dims D, const double2 *g, double2 *out) {
     }
 }
 
+// Pair-symmetric ladder blocks. For pair momentum s, representative pairs alpha = (ka, a, b)
+// (kb = s - ka) are listed in reps[s][.] as (ka * v + a) * v + b: first the n_minus[s] pairs with
+// ka*v+a < kb*v+b, then the fixed pairs (ka = kb, a = b). With Pi the pair swap,
+//   Wp[s][alpha][beta] = W(alpha, beta) + W(alpha, Pi beta)   (beta non-fixed), W(alpha, beta) (beta fixed)
+//   Wm[s][alpha][beta] = W(alpha, beta) - W(alpha, Pi beta)   (alpha, beta non-fixed)
+// zero-padded to Pp x Pp and Pm x Pm.
+__global__ void wpm_kernel(Dims D, const double2 *Wv, const int *reps, const int *npl, const int *nmi, int Pp, int Pm,
+                           double2 *Wp, double2 *Wm) {
+    const int v = D.v, nk = D.nk;
+    const i64 v2 = (i64)v * v, row = (i64)nk * v2;
+    const i64 totp = (i64)nk * Pp * Pp, totm = (i64)nk * Pm * Pm;
+    GRID_STRIDE(idx, totp + totm) {
+        const bool plus = idx < totp;
+        const i64 e = plus ? idx : idx - totp;
+        const int P = plus ? Pp : Pm;
+        const int s = (int)(e / ((i64)P * P));
+        const int al = (int)((e / P) % P), be = (int)(e % P);
+        const int nlim = plus ? npl[s] : nmi[s];
+        double2 out = make_double2(0, 0);
+        if (al < nlim && be < nlim) {
+            const int ra = reps[(i64)s * Pp + al], rb = reps[(i64)s * Pp + be];
+            const int ka = ra / (int)v2, a = (ra / v) % v, bb = ra % v;
+            const int kb = kminus(D, s, ka);
+            const int ke = rb / (int)v2, ee = (rb / v) % v, ff = rb % v;
+            const int kf = kminus(D, s, ke);
+            const i64 arow = (((i64)ka * nk + kb) * v2 + (i64)a * v + bb) * row;
+            const double2 w1 = Wv[arow + (i64)ke * v2 + (i64)ee * v + ff];
+            const bool fixed_be = (ke == kf && ee == ff);
+            if (fixed_be) out = w1;
+            else {
+                const double2 w2 = Wv[arow + (i64)kf * v2 + (i64)ff * v + ee];
+                out = plus ? cadd(w1, w2) : csub(w1, w2);
+            }
+        }
+        (plus ? Wp : Wm)[e] = out;
+    }
+}
+
 __global__ void to_float_kernel(const double2 *a, float2 *b, i64 n) {
     GRID_STRIDE(idx, n) b[idx] = make_float2((float)a[idx].x, (float)a[idx].y);
 }
@@ -535,6 +575,57 @@ ccgf_status build_intermediates(ccgf_handle *h, const ccgf_system *sys, cudaStre
     i64 nk3 = (i64)nk * nk * nk;
     CCGF_TRY(dalloc(W[BUF_WVVVV], nk3 * v * v * v * v));
     wvvvv_kernel<<<grid_for(W[BUF_WVVVV].n), 256, 0, st>>>(D, g.p, h->t2.p, W[BUF_WVVVV].p);
+    {
+        // representatives of the pair space of every pair momentum s (host), then W+ / W-
+        const int v2 = v * v;
+        std::vector<int> np(nk), nm(nk);
+        std::vector<std::vector<int>> lists(nk);
+        for (int s = 0; s < nk; ++s) {
+            std::vector<int> nonfixed, fixed;
+            for (int ka = 0; ka < nk; ++ka) {
+                const int kb = h->km.s(s, ka);
+                for (int a = 0; a < v; ++a)
+                    for (int bb = 0; bb < v; ++bb) {
+                        const int c1 = ka * v + a, c2 = kb * v + bb;
+                        if (c1 < c2) nonfixed.push_back((ka * v + a) * v + bb);
+                        else if (c1 == c2) fixed.push_back((ka * v + a) * v + bb);
+                    }
+            }
+            nm[s] = (int)nonfixed.size();
+            np[s] = (int)(nonfixed.size() + fixed.size());
+            lists[s] = nonfixed;
+            lists[s].insert(lists[s].end(), fixed.begin(), fixed.end());
+        }
+        int Pp = 0, Pm = 0;
+        for (int s = 0; s < nk; ++s) {
+            Pp = std::max(Pp, np[s]);
+            Pm = std::max(Pm, nm[s]);
+        }
+        Pp = std::max(Pp, 1);
+        Pm = std::max(Pm, 1);
+        std::vector<int> reps((size_t)nk * Pp, 0);
+        for (int s = 0; s < nk; ++s)
+            for (int i = 0; i < np[s]; ++i) reps[(size_t)s * Pp + i] = lists[s][i];
+        h->lad_np = np;
+        h->lad_nm = nm;
+        h->lad_Pp = Pp;
+        h->lad_Pm = Pm;
+        CCGF_TRY(dalloc(h->lad_reps, (i64)nk * Pp));
+        CCGF_TRY(dalloc(h->lad_npl, nk));
+        CCGF_TRY(dalloc(h->lad_nmi, nk));
+        CCGF_CUDA_TRY(cudaMemcpyAsync(h->lad_reps.p, reps.data(), sizeof(int) * reps.size(), cudaMemcpyHostToDevice, st));
+        CCGF_CUDA_TRY(cudaMemcpyAsync(h->lad_npl.p, np.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, st));
+        CCGF_CUDA_TRY(cudaMemcpyAsync(h->lad_nmi.p, nm.data(), sizeof(int) * nk, cudaMemcpyHostToDevice, st));
+        CCGF_TRY(dalloc(W[BUF_WPLUS], (i64)nk * Pp * Pp));
+        CCGF_TRY(dalloc(W[BUF_WMINUS], (i64)nk * Pm * Pm));
+        wpm_kernel<<<grid_for((i64)nk * (Pp * (i64)Pp + Pm * (i64)Pm)), 256, 0, st>>>(
+            D, W[BUF_WVVVV].p, h->lad_reps.p, h->lad_npl.p, h->lad_nmi.p, Pp, Pm, W[BUF_WPLUS].p, W[BUF_WMINUS].p);
+        h->launches++;
+        CCGF_CUDA_TRY(cudaGetLastError());
+        CCGF_CUDA_TRY(cudaStreamSynchronize(st));
+        dfree(W[BUF_WVVVV]);   // the ladder reads only W+ / W-
+        (void)v2;
+    }
     CCGF_TRY(dalloc(W[BUF_WVVVO], nk3 * o * v * v * v));
     wvvvo_kernel<<<grid_for(W[BUF_WVVVO].n), 256, 0, st>>>(D, g.p, h->t2.p, W[BUF_FOV].p, W[BUF_WVVVO].p);
     h->wov_seg = nk3 * o * o * v * v;

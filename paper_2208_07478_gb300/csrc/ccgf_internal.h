@@ -74,6 +74,10 @@ struct PermDesc {
     const i64 *offA, *offC;
     double2 alpha, beta;
 };
+// tcgen05 tensor-core path for FP32 operands (tc_gemm.cu): TF32 split, three MMAs per K-step;
+// *err is set to 1 when a bounded wait gives up (C is then left unwritten by that CTA)
+bool tc_zgemm_supported(const GemmDesc &d);
+int launch_tc_zgemm(const GemmDesc &d, const float2 *A, const float2 *B, float2 *C, int *err, cudaStream_t st);
 template <typename R>
 int launch_zpermute(const PermDesc &d, const typename cvec<R>::T *A, typename cvec<R>::T *C, cudaStream_t st);
 
@@ -92,7 +96,7 @@ struct KMeshH {
 // A sigma plan is a list of launches over fixed buffers: A operands are
 // intermediates (buffer ids below), B operands always live in the scratch arena
 // (the input vector is copied there first), C operands are the output or scratch.
-enum { STEP_GEMM = 0, STEP_PERM = 1, STEP_FOV_IP = 2, STEP_FOV_EA = 3 };
+enum { STEP_GEMM = 0, STEP_PERM = 1, STEP_FOV_IP = 2, STEP_FOV_EA = 3, STEP_LADDER_GATHER = 4, STEP_LADDER_SCATTER = 5 };
 struct SigmaStep {
     const char *name;
     int kind;
@@ -101,6 +105,7 @@ struct SigmaStep {
     int a_buf;         // GEMM: intermediate id (or BUF_SCRATCH); PERM: source (BUF_SCRATCH)
     int c_buf;         // BUF_Y or BUF_SCRATCH
     i64 offA_pos, offB_pos, offC_pos;   // positions in the plan's offset table
+    i64 lad_rp, lad_rm;                 // ladder gather / scatter: scratch offsets of R+ / S+ and R- / S-
 };
 struct SigmaPlan {
     int sector, K, nv;
@@ -114,7 +119,7 @@ struct SigmaPlan {
 enum {
     BUF_Y = 0, BUF_SCRATCH,
     BUF_FOO, BUF_FVV, BUF_FOV,
-    BUF_WVVVV, BUF_WVVVO, BUF_WOV3, BUF_UVOVV, BUF_UOOVV_EA, BUF_T2EA,
+    BUF_WVVVV, BUF_WPLUS, BUF_WMINUS, BUF_WVVVO, BUF_WOV3, BUF_UVOVV, BUF_UOOVV_EA, BUF_T2EA,
     BUF_WOVOO, BUF_WOOOO, BUF_UOOOV, BUF_UOOVV_IP, BUF_T2IP,
     NBUF
 };
@@ -133,9 +138,15 @@ struct ccgf_handle {
     DBuf<double2> W[NBUF];
     DBuf<float2> Wf[NBUF];
     i64 wov_seg;       // size of each of W1 | W2 | WN inside BUF_WOV3
+    // pair-symmetric EA ladder: representatives per pair momentum and padded block sizes
+    std::vector<int> lad_np, lad_nm;
+    int lad_Pp = 0, lad_Pm = 0;
+    DBuf<int> lad_reps, lad_npl, lad_nmi;
     // scratch arena for sigma (FP64 and FP32 variants) and the FP32 output
     DBuf<double2> scratch;
     DBuf<float2> scratch_f, yf;
+    // error flag of the tensor-core GEMMs (allocated on first CCGF_TF32X3 use)
+    DBuf<int> tc_err;
     // cached plans, index (sector-1)*nk + K, valid for plan_nv columns
     std::vector<SigmaPlan *> plans;
     int plan_nv = 0;
@@ -157,6 +168,8 @@ const char *plan_step_name(const ccgf_handle *h, int sector, int K, int step);
 ccgf_status sigma_apply(ccgf_handle *h, int sector, int K, int nv, const double2 *x, double2 *y,
                         ccgf_precision prec, cudaStream_t st);
 void free_plans(ccgf_handle *h);
+// reads and clears the tensor-core error flag (synchronises st); CCGF_ERR_TIMEOUT when it was set
+ccgf_status tc_error_check(ccgf_handle *h, cudaStream_t st);
 ccgf_status sigma_apply_in_arena(ccgf_handle *h, int sector, int K, int nv, const double2 *x, double2 *y, double2 *arena,
                                  i64 arena_elems, i64 *offsets, i64 offsets_cap, cudaStream_t st);
 i64 sigma_arena_elems(const ccgf_handle *h, int nv);

@@ -310,7 +310,6 @@ __global__ void apply_kernel(const float *Y, const double2 *Base, const double *
         if (Xbase) Xbase[mu0 * nv + r] = Base[r];
     }
 }
-// training rows: random (mu, p) of interior training frequency i, features from i-1 / i+1, target i
 __device__ __forceinline__ unsigned hash32(unsigned x) {
     x ^= x >> 16;
     x *= 0x7feb352dU;
@@ -319,20 +318,6 @@ __device__ __forceinline__ unsigned hash32(unsigned x) {
     x ^= x >> 16;
     return x;
 }
-__global__ void train_rows_kernel(FeatArgs a, int i, unsigned seed, i64 rows, float *Fm, float *T) {
-    for (i64 r = (i64)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (i64)gridDim.x * blockDim.x) {
-        unsigned h1 = hash32(seed ^ (unsigned)(r * 2654435761u)), h2 = hash32(h1 + 0x9e3779b9u);
-        const i64 mu = (i64)(((unsigned long long)h1 * (unsigned long long)a.D) >> 32);   // uniform in [0, D)
-        const int p = (int)(((unsigned long long)h2 * (unsigned long long)a.N) >> 32);
-        double2 base;
-        feat_row(a, mu, p, 0, Fm + r * kF, &base);
-        const double2 x = a.store[((i64)i * a.D + mu) * a.N + p];
-        const double sc = a.eta / (a.bnorm[p] > 0 ? a.bnorm[p] : 1.0);
-        T[2 * r] = (float)(sc * (x.x - base.x));
-        T[2 * r + 1] = (float)(sc * (x.y - base.y));
-    }
-}
-
 // training rows mixed over k-points and interior training frequencies of one sector:
 // row r draws (K, i, mu, p); store_all [nk][n][D][N], d_all [nk][D], bnorm_all [nk][N]
 __global__ void train_rows_mixed_kernel(FeatArgs a, int nk, int n, const double2 *store_all, const double *d_all,
@@ -568,17 +553,8 @@ ccgf_status warmstart_train(ccgf_handle *h, int sectors, int steps, i64 rows, do
     std::vector<int> secs;
     for (int sec = 1; sec <= 2; ++sec)
         if (sectors & sec) secs.push_back(sec);
-    DBuf<double> dvec;
-    i64 Dmax = std::max(h->dim_ip, h->dim_ea);
-    CCGF_TRY(dalloc(dvec, Dmax));
-    DBuf<int> dlo, dhi;
-    DBuf<double> dom;
-    CCGF_TRY(dalloc(dlo, 1));
-    CCGF_TRY(dalloc(dhi, 1));
-    CCGF_TRY(dalloc(dom, 1));
     const float b1 = 0.9f, b2 = 0.999f;
     double last = 0;
-    // one mini-batch of training rows of a (sector, K, interior i) chosen from the step index
     // diagonal estimates of every (sector, K), kept for the whole training
     DBuf<double> dall[2];
     for (int sec : secs) {
@@ -684,10 +660,8 @@ ccgf_status warmstart_train(ccgf_handle *h, int sectors, int steps, i64 rows, do
     }
     CCGF_CUDA_TRY(cudaGetLastError());
     CCGF_CUDA_TRY(cudaStreamSynchronize(st));
-    dfree(dvec);
-    dfree(dlo);
-    dfree(dhi);
-    dfree(dom);
+    dfree(dall[0]);
+    dfree(dall[1]);
     w->trained = true;
     if (final_loss) *final_loss = w->use_net ? vnet : vbase;
     return CCGF_OK;

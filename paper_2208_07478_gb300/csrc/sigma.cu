@@ -236,33 +236,35 @@ SigmaPlan *build_plan_ea(const ccgf_handle *h, int K, int nv) {
             }
         B.gemm((int)ov, (int)(v * NV), (int)ov, nk, BUF_WOV3, ov, 1, oA, v * NV, 1, oB, BUF_Y, v * NV, 1, oC, 1.0, 1.0);
     }
-    // ladder: XT[kj][ke][e][f][j] = r2[kj,ke][j,e,f];  T3[kj][ka][a][b][j] = Wvvvv[ka,kb] XT[kj];  s2 += T3
+    // ladder (pair-symmetric): R+/- on pair representatives of every pair momentum s = K + kj,
+    // S+/- = W+/-[s] R+/-[s], then S(alpha) = S+ + S-, S(Pi alpha) = S+ - S- scattered into s2
     B.cur = "ea_ladder_wvvvv";
     {
-        std::vector<i64> oA, oC;
-        for (int kj = 0; kj < nk; ++kj)
-            for (int ke = 0; ke < nk; ++ke) {
-                oA.push_back(sx + row(kj, ke) * NV);
-                oC.push_back(P->seg[SEG_XT] + ((i64)kj * nk + ke) * S2 * NV);
-            }
-        B.perm({v, v, o, NV}, {v * NV, NV, v2 * NV, 1}, oA, BUF_SCRATCH, {o * v * NV, o * NV, NV, 1}, oC, 1.0, 0.0);
-        std::vector<i64> gA, gB, gC;
-        for (int kj = 0; kj < nk; ++kj)
-            for (int ka = 0; ka < nk; ++ka) {
-                int kb = km.c(K, ka, kj);
-                gA.push_back(((i64)ka * nk + kb) * v2 * nk * v2);
-                gB.push_back(P->seg[SEG_XT] + (i64)kj * nk * S2 * NV);
-                gC.push_back(P->seg[SEG_T3] + ((i64)kj * nk + ka) * S2 * NV);
-            }
-        B.gemm((int)v2, (int)(o * NV), (int)(nk * v2), 1, BUF_WVVVV, nk * v2, 1, gA, o * NV, 1, gB, BUF_SCRATCH, o * NV, 1, gC,
-               1.0, 0.0);
-        std::vector<i64> pA, pC;
-        for (int kj = 0; kj < nk; ++kj)
-            for (int ka = 0; ka < nk; ++ka) {
-                pA.push_back(P->seg[SEG_T3] + ((i64)kj * nk + ka) * S2 * NV);
-                pC.push_back(row(kj, ka) * NV);
-            }
-        B.perm({v, v, o, NV}, {v * o * NV, o * NV, NV, 1}, pA, BUF_Y, {v * NV, NV, v2 * NV, 1}, pC, 1.0, 1.0);
+        const int Pp = h->lad_Pp, Pm = h->lad_Pm;
+        const i64 on = (i64)o * NV;
+        SigmaStep g{};
+        g.name = B.cur;
+        g.kind = STEP_LADDER_GATHER;
+        g.lad_rp = P->seg[SEG_XT];
+        g.lad_rm = P->seg[SEG_R];
+        P->steps.push_back(g);
+        std::vector<i64> aP, bP, cP, aM, bM, cM;
+        for (int sp = 0; sp < nk; ++sp) {
+            aP.push_back((i64)sp * Pp * Pp);
+            bP.push_back(P->seg[SEG_XT] + (i64)sp * Pp * on);
+            cP.push_back(P->seg[SEG_T3] + (i64)sp * Pp * on);
+            aM.push_back((i64)sp * Pm * Pm);
+            bM.push_back(P->seg[SEG_R] + (i64)sp * Pm * on);
+            cM.push_back(P->seg[SEG_T1] + (i64)sp * Pm * on);
+        }
+        B.gemm(Pp, (int)on, Pp, 1, BUF_WPLUS, Pp, 1, aP, on, 1, bP, BUF_SCRATCH, on, 1, cP, 1.0, 0.0);
+        B.gemm(Pm, (int)on, Pm, 1, BUF_WMINUS, Pm, 1, aM, on, 1, bM, BUF_SCRATCH, on, 1, cM, 1.0, 0.0);
+        SigmaStep sc{};
+        sc.name = B.cur;
+        sc.kind = STEP_LADDER_SCATTER;
+        sc.lad_rp = P->seg[SEG_T3];
+        sc.lad_rm = P->seg[SEG_T1];
+        P->steps.push_back(sc);
     }
     // three-body: Ysm[m] = sum (2<mn|ef> - <mn|fe>) r2[kn,ke][n,e,f];  s2 -= t2[K,kj,ka][m,j,a,b] Ysm[m]
     B.cur = "ea_threebody";
@@ -509,6 +511,65 @@ __global__ void fov_kernel(int sector, int K, int nk, int o, int v, int nv, cons
     y[(i64)p * nv + c] = out;
 }
 
+// EA ladder, pair-symmetric form. Pair representatives reps[s][beta] = (ke * v + e) * v + f,
+// first nmi[s] non-fixed pairs, then the fixed ones (ke = kf, e = f); kj = s - K.
+template <typename T, typename R>
+__global__ void ladder_gather_kernel(int K, int nk, int o, int v, int nv, const int *ksub, const int *reps, const int *npl,
+                                     const int *nmi, int Pp, int Pm, const T *__restrict__ x, T *__restrict__ Rp,
+                                     T *__restrict__ Rm) {
+    const i64 S2 = (i64)o * v * v, total = (i64)nk * Pp * o * nv;
+    for (i64 idx = (i64)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (i64)gridDim.x * blockDim.x) {
+        const int vec = idx % nv, j = (idx / nv) % o;
+        const int be = (int)((idx / ((i64)nv * o)) % Pp), s = (int)(idx / ((i64)nv * o * Pp));
+        const int kj = ksub[s * nk + K];
+        T rp, rm;
+        rp.x = rp.y = rm.x = rm.y = 0;
+        if (be < npl[s]) {
+            const int rep = reps[(i64)s * Pp + be];
+            const int ke = rep / (v * v), e = (rep / v) % v, f = rep % v, kf = ksub[s * nk + ke];
+            const T r1 = x[(v + ((i64)kj * nk + ke) * S2 + ((i64)j * v + e) * v + f) * nv + vec];
+            if (be < nmi[s]) {
+                const T r2 = x[(v + ((i64)kj * nk + kf) * S2 + ((i64)j * v + f) * v + e) * nv + vec];
+                rp.x = (R)0.5 * (r1.x + r2.x);
+                rp.y = (R)0.5 * (r1.y + r2.y);
+                rm.x = (R)0.5 * (r1.x - r2.x);
+                rm.y = (R)0.5 * (r1.y - r2.y);
+            } else {
+                rp = r1;
+            }
+        }
+        Rp[(((i64)s * Pp + be) * o + j) * nv + vec] = rp;
+        if (be < Pm) Rm[(((i64)s * Pm + be) * o + j) * nv + vec] = rm;
+    }
+}
+template <typename T, typename R>
+__global__ void ladder_scatter_kernel(int K, int nk, int o, int v, int nv, const int *ksub, const int *reps, const int *npl,
+                                      const int *nmi, int Pp, int Pm, const T *__restrict__ Sp, const T *__restrict__ Sm,
+                                      T *__restrict__ y) {
+    const i64 S2 = (i64)o * v * v, total = (i64)nk * Pp * o * nv;
+    for (i64 idx = (i64)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (i64)gridDim.x * blockDim.x) {
+        const int vec = idx % nv, j = (idx / nv) % o;
+        const int al = (int)((idx / ((i64)nv * o)) % Pp), s = (int)(idx / ((i64)nv * o * Pp));
+        if (al >= npl[s]) continue;
+        const int kj = ksub[s * nk + K];
+        const int rep = reps[(i64)s * Pp + al];
+        const int ka = rep / (v * v), a = (rep / v) % v, b = rep % v, kb = ksub[s * nk + ka];
+        const T sp = Sp[(((i64)s * Pp + al) * o + j) * nv + vec];
+        T sm;
+        sm.x = sm.y = 0;
+        const bool nonfixed = al < nmi[s];
+        if (nonfixed) sm = Sm[(((i64)s * Pm + al) * o + j) * nv + vec];
+        T *y1 = y + (v + ((i64)kj * nk + ka) * S2 + ((i64)j * v + a) * v + b) * nv + vec;
+        y1->x += sp.x + sm.x;
+        y1->y += sp.y + sm.y;
+        if (nonfixed) {
+            T *y2 = y + (v + ((i64)kj * nk + kb) * S2 + ((i64)j * v + b) * v + a) * nv + vec;
+            y2->x += sp.x - sm.x;
+            y2->y += sp.y - sm.y;
+        }
+    }
+}
+
 template <typename R> using T_arena = typename cvec<R>::T *;
 
 template <typename R>
@@ -530,7 +591,8 @@ inline unsigned gsz(i64 n) {
 }
 
 template <typename R>
-void run_plan(ccgf_handle *h, SigmaPlan *P, const double2 *x, double2 *y, cudaStream_t st, T_arena<R> arena = nullptr) {
+void run_plan(ccgf_handle *h, SigmaPlan *P, const double2 *x, double2 *y, cudaStream_t st, T_arena<R> arena = nullptr,
+              bool tensor_cores = false) {
     typedef typename cvec<R>::T T;
     const bool f64 = sizeof(R) == 8;
     T *scr = arena ? arena : (f64 ? (T *)h->scratch.p : (T *)h->scratch_f.p);
@@ -552,12 +614,29 @@ void run_plan(ccgf_handle *h, SigmaPlan *P, const double2 *x, double2 *y, cudaSt
             d.offB = offs + s.offB_pos;
             d.offC = offs + s.offC_pos;
             const T *A = f64 ? (const T *)h->W[s.a_buf].p : (const T *)h->Wf[s.a_buf].p;
+            if constexpr (sizeof(R) == 4) {
+                if (tensor_cores && tc_zgemm_supported(d)) {
+                    h->launches += launch_tc_zgemm(d, A, scr, C, h->tc_err.p, st);
+                    continue;
+                }
+            }
             h->launches += launch_zgemm<R>(d, A, scr, C, st, scr + P->seg[SEG_SPLITK], P->seg[SEG_END] - P->seg[SEG_SPLITK]);
         } else if (s.kind == STEP_PERM) {
             PermDesc d = s.p;
             d.offA = offs + s.offA_pos;
             d.offC = offs + s.offC_pos;
             h->launches += launch_zpermute<R>(d, scr, C, st);
+        } else if (s.kind == STEP_LADDER_GATHER || s.kind == STEP_LADDER_SCATTER) {
+            const i64 total = (i64)h->nk * h->lad_Pp * h->o * P->nv;
+            if (s.kind == STEP_LADDER_GATHER)
+                ladder_gather_kernel<T, R><<<gsz(total), 256, 0, st>>>(P->K, h->nk, h->o, h->v, P->nv, h->ksub_d.p, h->lad_reps.p,
+                                                                     h->lad_npl.p, h->lad_nmi.p, h->lad_Pp, h->lad_Pm,
+                                                                     scr + P->seg[SEG_X], scr + s.lad_rp, scr + s.lad_rm);
+            else
+                ladder_scatter_kernel<T, R><<<gsz(total), 256, 0, st>>>(P->K, h->nk, h->o, h->v, P->nv, h->ksub_d.p, h->lad_reps.p,
+                                                                      h->lad_npl.p, h->lad_nmi.p, h->lad_Pp, h->lad_Pm,
+                                                                      scr + s.lad_rp, scr + s.lad_rm, yout);
+            h->launches++;
         } else {
             const int sector = s.kind == STEP_FOV_IP ? CCGF_SECTOR_IP : CCGF_SECTOR_EA;
             const int nrow = sector == CCGF_SECTOR_IP ? h->o : h->v;
@@ -598,6 +677,19 @@ bool check_plan(const ccgf_handle *h, const SigmaPlan *P, const std::vector<i64>
                 }
                 i64 oc = off[s.offC_pos + b];
                 if (oc < 0 || oc + spanC >= clen) { why = "gemm C out of range at step " + std::to_string(si); return false; }
+            }
+        } else if (s.kind == STEP_LADDER_GATHER || s.kind == STEP_LADDER_SCATTER) {
+            // segments: R+/S+ need nk Pp nocc nv, R-/S- need nk Pm nocc nv elements; x2 / y2 indices
+            // come from representatives of the pair space, all inside [nvir, dim_ea) rows
+            const i64 need_p = (i64)h->nk * h->lad_Pp * h->o * P->nv, need_m = (i64)h->nk * h->lad_Pm * h->o * P->nv;
+            auto seg_len = [&](i64 off) -> i64 {
+                for (int g = 0; g < SEG_END; ++g)
+                    if (P->seg[g] == off) return P->seg[g + 1] - off;
+                return -1;
+            };
+            if (P->sector != CCGF_SECTOR_EA || seg_len(s.lad_rp) < need_p || seg_len(s.lad_rm) < need_m) {
+                why = "ladder segment too small at step " + std::to_string(si);
+                return false;
             }
         } else if (s.kind == STEP_PERM) {
             const PermDesc &p = s.p;
@@ -697,9 +789,27 @@ ccgf_status sigma_apply(ccgf_handle *h, int sector, int K, int nv, const double2
                 CCGF_TRY(dalloc(h->yf, dmax * nv));
             }
         }
-        run_plan<float>(h, P, x, y, st);
+        const bool tc = prec == CCGF_TF32X3;
+        if (tc && !h->tc_err.p) {
+            CCGF_TRY(dalloc(h->tc_err, 1));
+            CCGF_CUDA_TRY(cudaMemset(h->tc_err.p, 0, sizeof(int)));
+        }
+        run_plan<float>(h, P, x, y, st, nullptr, tc);
     }
     CCGF_CUDA_TRY(cudaGetLastError());
+    return CCGF_OK;
+}
+
+ccgf_status tc_error_check(ccgf_handle *h, cudaStream_t st) {
+    if (!h->tc_err.p) return CCGF_OK;
+    int flag = 0;
+    CCGF_CUDA_TRY(cudaMemcpyAsync(&flag, h->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CCGF_CUDA_TRY(cudaStreamSynchronize(st));
+    if (flag) {
+        CCGF_CUDA_TRY(cudaMemsetAsync(h->tc_err.p, 0, sizeof(int), st));
+        set_last_error("a tensor-core GEMM wait exceeded its 2 s limit; its output tile was not written");
+        return CCGF_ERR_TIMEOUT;
+    }
     return CCGF_OK;
 }
 

@@ -613,5 +613,6 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
     cudaEventDestroy(ev1);
     cudaEventDestroy(es0);
     cudaEventDestroy(es1);
+    if (opt->prec == CCGF_TF32X3) CCGF_TRY(tc_error_check(h, st));
     return final_status;
 }

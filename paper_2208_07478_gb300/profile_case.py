@@ -23,7 +23,7 @@ def main():
     ap.add_argument("--naux", type=int, default=64)
     ap.add_argument("--nvec", type=int, default=0, help="default: nocc + nvir")
     ap.add_argument("--sector", default="ea", choices=["ip", "ea"])
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "tf32x3"])
     ap.add_argument("--calls", type=int, default=1)
     a = ap.parse_args()
     import torch
@@ -36,7 +36,7 @@ def main():
     nvec = a.nvec or s.nmo
     x = torch.randn((nvec, D), dtype=torch.complex128, device="cuda")
     y = torch.empty_like(x)
-    prec = B.FP64 if a.prec == "fp64" else B.FP32
+    prec = {"fp64": B.FP64, "fp32": B.FP32, "tf32x3": B.TF32X3}[a.prec]
     fn = B.sigma_ea if a.sector == "ea" else B.sigma_ip
     fn(h, 0, x, y, prec=prec)
     for _ in range(a.calls):
