@@ -46,6 +46,7 @@ class Stats(C.Structure):
 
 EXPORTS = ["ccgf_default_options", "ccgf_build_intermediates", "ccgf_dims", "ccgf_sigma_ip", "ccgf_sigma_ea",
            "ccgf_rhs", "ccgf_left", "ccgf_solve_gf", "ccgf_sigma_profile", "ccgf_sigma_step_name", "ccgf_sigma_ip_noalloc", "ccgf_launch_count",
+           "ccgf_set_autotune", "ccgf_sigma_step_kernel",
            "ccgf_train_warmstart", "ccgf_mlp_param_count", "ccgf_mlp_forward", "ccgf_mlp_loss_grad", "ccgf_destroy",
            "ccgf_status_string", "ccgf_last_error"]
 
@@ -93,6 +94,10 @@ def load(path: str | None = None):
     lib.ccgf_mlp_loss_grad.restype = i
     lib.ccgf_launch_count.argtypes = [vp]
     lib.ccgf_launch_count.restype = ll
+    lib.ccgf_set_autotune.argtypes = [C.c_int]
+    lib.ccgf_set_autotune.restype = None
+    lib.ccgf_sigma_step_kernel.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int]
+    lib.ccgf_sigma_step_kernel.restype = C.c_int
     lib.ccgf_destroy.argtypes = [vp]
     lib.ccgf_destroy.restype = None
     lib.ccgf_status_string.argtypes = [i]
@@ -166,6 +171,10 @@ class Handle:
     def launch_count(self):
         return int(load().ccgf_launch_count(self.ptr))
 
+    def step_kernel(self, sector, kshift, step, prec):
+        """Kernel chosen for a plan step (see ccgf_sigma_step_kernel)."""
+        return int(load().ccgf_sigma_step_kernel(self.ptr, sector, kshift, step, prec))
+
     def dims(self):
         nk, o, v = C.c_int(), C.c_int(), C.c_int()
         dip, dea = C.c_longlong(), C.c_longlong()
@@ -199,6 +208,14 @@ def sigma_ip(h: Handle, kshift, x, y, prec=FP64, stream=None):
 def sigma_ea(h: Handle, kshift, x, y, prec=FP64, stream=None):
     nvec = x.shape[0] if x.ndim == 2 else 1
     return _check(load().ccgf_sigma_ea(h.ptr, kshift, nvec, _ptr(x), _ptr(y), prec, _stream_ptr(stream)))
+
+
+def set_autotune(enable: bool):
+    """Measured kernel choice per contraction on (default) or off (model defaults); process-wide."""
+    load().ccgf_set_autotune(1 if enable else 0)
+
+
+KERNEL_TC_TMA, KERNEL_TC_REG = 100, 101
 
 
 def sigma_ip_noalloc(h: Handle, kshift, x, y, stream=None):
@@ -236,7 +253,8 @@ def mlp_loss_grad(F, H, theta, X, T, grad, bf16=True, stream=None):
 
 
 def sigma_profile(h: Handle, sector, kshift, x, y, prec=FP64, stream=None, max_steps=64):
-    """One sigma call with per-step device times; returns [(name, ms, flops)]."""
+    """One sigma call with per-step device times; returns [(name, ms, flops, kernel)] with kernel
+    the choice code of ccgf_sigma_step_kernel (-1 for steps that are not contractions)."""
     nvec = x.shape[0] if x.ndim == 2 else 1
     ms = (C.c_double * max_steps)()
     fl = (C.c_double * max_steps)()
@@ -244,7 +262,8 @@ def sigma_profile(h: Handle, sector, kshift, x, y, prec=FP64, stream=None, max_s
     lib = load()
     _check(lib.ccgf_sigma_profile(h.ptr, sector, kshift, nvec, _ptr(x), _ptr(y), prec, _stream_ptr(stream), max_steps,
                                   ms, fl, C.byref(n)))
-    return [(lib.ccgf_sigma_step_name(h.ptr, sector, kshift, k).decode(), ms[k], fl[k]) for k in range(min(n.value, max_steps))]
+    return [(lib.ccgf_sigma_step_name(h.ptr, sector, kshift, k).decode(), ms[k], fl[k],
+             int(lib.ccgf_sigma_step_kernel(h.ptr, sector, kshift, k, prec))) for k in range(min(n.value, max_steps))]
 
 
 def rhs(h: Handle, sector, K, p, out, stream=None):

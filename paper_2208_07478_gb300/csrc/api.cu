@@ -39,6 +39,7 @@ void destroy(ccgf_handle *h) {
     dfree(h->scratch_f);
     dfree(h->yf);
     dfree(h->tc_err);
+    tc_free(h);
     delete h;
 }
 
@@ -227,6 +228,12 @@ const char *ccgf_sigma_step_name(const ccgf_handle *h, int sector, int kshift, i
 }
 
 long long ccgf_launch_count(const ccgf_handle *h) { return h ? h->launches : 0; }
+
+void ccgf_set_autotune(int enable) { set_autotune(enable != 0); }
+int ccgf_sigma_step_kernel(const ccgf_handle *h, int sector, int kshift, int step, ccgf_precision prec) {
+    if (!h || (int)prec < 0 || (int)prec > 2) return -1;
+    return plan_step_choice(h, sector, kshift, step, (int)prec);
+}
 
 ccgf_status ccgf_train_warmstart(ccgf_handle *h, int sectors, int n_train, const double *omega_train, double eta,
                                  const ccgf_options *opt, int steps, long long rows_per_step, double lr, unsigned seed,

@@ -53,7 +53,9 @@ struct GemmDesc {
     i64 rsA, csA, rsB, csB, rsC, csC;
     const i64 *offA, *offB, *offC;   // device offset tables
     double2 alpha, beta;
+    int tile;                        // SIMT per-thread tile: 0 = the launcher's model choice, k = its k-th candidate
 };
+int zgemm_tile_count();              // number of SIMT tile candidates
 // Long-K GEMMs with few output tiles split K across CTAs (deterministic: partial sums go to
 // `work`, then one reduction applies alpha / beta); work may be NULL (no split).
 int zgemm_ksplit(const GemmDesc &d);
@@ -78,6 +80,12 @@ struct PermDesc {
 // *err is set to 1 when a bounded wait gives up (C is then left unwritten by that CTA)
 bool tc_zgemm_supported(const GemmDesc &d);
 int launch_tc_zgemm(const GemmDesc &d, const float2 *A, const float2 *B, float2 *C, int *err, cudaStream_t st);
+struct ccgf_handle;
+// TMA-fed variant: A = intermediate a_buf, read through tensor maps over its TF32 hi / lo copies
+// (tc_prepare); rowA[b * nred + r] = offA / rsA. Returns 0 (nothing launched) when the shape or
+// buffer does not qualify, else the number of launches.
+int launch_tc_zgemm_tma(ccgf_handle *h, int a_buf, const GemmDesc &d, const i64 *rowA, const float2 *B, float2 *C, int *err,
+                        cudaStream_t st);
 template <typename R>
 int launch_zpermute(const PermDesc &d, const typename cvec<R>::T *A, typename cvec<R>::T *C, cudaStream_t st);
 
@@ -106,6 +114,8 @@ struct SigmaStep {
     int c_buf;         // BUF_Y or BUF_SCRATCH
     i64 offA_pos, offB_pos, offC_pos;   // positions in the plan's offset table
     i64 lad_rp, lad_rm;                 // ladder gather / scatter: scratch offsets of R+ / S+ and R- / S-
+    i64 rowA_pos;                       // GEMM: position of offA / rsA per (batch, reduction), -1 if not integral
+    int choice[3];                      // GEMM kernel measured per precision (0 = not tuned; see sigma.cu)
 };
 struct SigmaPlan {
     int sector, K, nv;
@@ -145,8 +155,9 @@ struct ccgf_handle {
     // scratch arena for sigma (FP64 and FP32 variants) and the FP32 output
     DBuf<double2> scratch;
     DBuf<float2> scratch_f, yf;
-    // error flag of the tensor-core GEMMs (allocated on first CCGF_TF32X3 use)
+    // error flag of the tensor-core GEMMs and their TF32-split operands (made on first CCGF_TF32X3 use)
     DBuf<int> tc_err;
+    void *tc_ops = nullptr;
     // cached plans, index (sector-1)*nk + K, valid for plan_nv columns
     std::vector<SigmaPlan *> plans;
     int plan_nv = 0;
@@ -168,8 +179,13 @@ const char *plan_step_name(const ccgf_handle *h, int sector, int K, int step);
 ccgf_status sigma_apply(ccgf_handle *h, int sector, int K, int nv, const double2 *x, double2 *y,
                         ccgf_precision prec, cudaStream_t st);
 void free_plans(ccgf_handle *h);
+void set_autotune(bool on);
+int plan_step_choice(const ccgf_handle *h, int sector, int K, int step, int prec_index);
 // reads and clears the tensor-core error flag (synchronises st); CCGF_ERR_TIMEOUT when it was set
 ccgf_status tc_error_check(ccgf_handle *h, cudaStream_t st);
+// tc_gemm.cu: TF32 hi / lo copies of every FP32 intermediate, freed by tc_free
+ccgf_status tc_prepare(ccgf_handle *h, cudaStream_t st);
+void tc_free(ccgf_handle *h);
 ccgf_status sigma_apply_in_arena(ccgf_handle *h, int sector, int K, int nv, const double2 *x, double2 *y, double2 *arena,
                                  i64 arena_elems, i64 *offsets, i64 offsets_cap, cudaStream_t st);
 i64 sigma_arena_elems(const ccgf_handle *h, int nv);

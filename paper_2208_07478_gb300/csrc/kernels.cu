@@ -191,7 +191,10 @@ static const TileShape kShapes[] = {{4, 4}, {3, 4}, {2, 4}, {4, 3}, {4, 2}, {4, 
 
 // Shape with the least padded work divided by the wave efficiency (whole waves of one CTA per
 // SM), with a slight preference for larger tiles (higher register reuse).
+int zgemm_tile_count() { return (int)(sizeof(kShapes) / sizeof(kShapes[0])); }
+
 static TileShape pick_shape(const GemmDesc &d) {
+    if (d.tile > 0 && d.tile <= zgemm_tile_count()) return kShapes[d.tile - 1];
     TileShape best = kShapes[0];
     double best_cost = 1e300;
     for (const TileShape &s : kShapes) {

@@ -18,6 +18,11 @@
 // built once per (sector, K, nv) and replayed on every call; the same plan runs
 // on the FP64 intermediates or on their FP32 copies.
 #include "ccgf_internal.h"
+#include <atomic>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 namespace {
 
@@ -54,6 +59,16 @@ struct PlanBuilder {
         s.offA_pos = push(oA);
         s.offB_pos = push(oB);
         s.offC_pos = push(oC);
+        // row coordinates of the A blocks for the TMA-fed tensor-core path
+        s.rowA_pos = -1;
+        if (csA == 1 && rsA > 0) {
+            std::vector<i64> rows;
+            for (i64 a : oA) {
+                if (a % rsA) break;
+                rows.push_back(a / rsA);
+            }
+            if (rows.size() == oA.size()) s.rowA_pos = push(rows);
+        }
         P->steps.push_back(s);
     }
     // dims (outer..inner), source strides (scratch), destination strides
@@ -590,11 +605,131 @@ inline unsigned gsz(i64 n) {
     return (unsigned)(g > 152 * 32 ? 152 * 32 : (g > 0 ? g : 1));
 }
 
+// GEMM kernel choices of a plan step: 0 = default (tensor cores through TMA when the operand
+// qualifies, else the register-fed tensor-core kernel; SIMT tile by the launcher's model),
+// k in 1..zgemm_tile_count() = SIMT kernel with the launcher's k-th tile, or one of these two
+enum { CHOICE_TC_TMA = 100, CHOICE_TC_REG = 101 };
+
+// one GEMM step with the given choice; returns the number of launches (0: choice not applicable)
+template <typename R>
+int run_gemm_step(ccgf_handle *h, const SigmaPlan *P, const SigmaStep &s, int choice, bool tensor_cores,
+                  typename cvec<R>::T *scr, typename cvec<R>::T *yout, cudaStream_t st) {
+    typedef typename cvec<R>::T T;
+    const bool f64 = sizeof(R) == 8;
+    const i64 *offs = P->offsets.p;
+    T *C = s.c_buf == BUF_Y ? yout : scr;
+    GemmDesc d = s.g;
+    d.offA = offs + s.offA_pos;
+    d.offB = offs + s.offB_pos;
+    d.offC = offs + s.offC_pos;
+    const T *A = f64 ? (const T *)h->W[s.a_buf].p : (const T *)h->Wf[s.a_buf].p;
+    if constexpr (sizeof(R) == 4) {
+        if (tensor_cores && tc_zgemm_supported(d) && (choice == 0 || choice >= CHOICE_TC_TMA)) {
+            int n = 0;
+            if ((choice == 0 || choice == CHOICE_TC_TMA) && s.rowA_pos >= 0)
+                n = launch_tc_zgemm_tma(h, s.a_buf, d, offs + s.rowA_pos, scr, C, h->tc_err.p, st);
+            if (n == 0 && choice != CHOICE_TC_TMA) n = launch_tc_zgemm(d, A, scr, C, h->tc_err.p, st);
+            return n;
+        }
+    }
+    if (choice >= CHOICE_TC_TMA) return 0;
+    d.tile = choice;
+    return launch_zgemm<R>(d, A, scr, C, st, scr + P->seg[SEG_SPLITK], P->seg[SEG_END] - P->seg[SEG_SPLITK]);
+}
+
+// Measured kernel choice per GEMM step (an autotuner): every candidate (the SIMT tiles and, for
+// CCGF_TF32X3, the two tensor-core kernels) runs once to warm up and twice timed with CUDA
+// events on the real operands; the fastest is kept in the step and in a process-wide table keyed
+// by the GEMM's shape, strides and precision, so later plans and handles reuse it without timing.
+// Runs before the plan's first execution, when the scratch arena and the output hold no live data
+// (every plan step writes its outputs before it reads them). CCGF_AUTOTUNE=0 keeps the defaults.
+struct TuneKey {
+    int pi, a_buf, M, N, K, nred, batch, tma;
+    i64 rsA, csA, rsB, csB, rsC, csC;
+    bool beta;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(pi, a_buf, M, N, K, nred, batch, tma, rsA, csA, rsB, csB, rsC, csC, beta) <
+               std::tie(o.pi, o.a_buf, o.M, o.N, o.K, o.nred, o.batch, o.tma, o.rsA, o.csA, o.rsB, o.csB, o.rsC, o.csC, o.beta);
+    }
+};
+std::map<TuneKey, int> g_tuned;
+std::mutex g_tuned_mu;
+
+std::atomic<int> g_autotune{-1};   // -1: not read yet, then 0 / 1
+bool autotune_enabled() {
+    int v = g_autotune.load();
+    if (v < 0) {
+        const char *e = std::getenv("CCGF_AUTOTUNE");
+        int want = (e && e[0] == '0') ? 0 : 1;
+        g_autotune.compare_exchange_strong(v, want);
+        v = g_autotune.load();
+    }
+    return v != 0;
+}
+
+template <typename R>
+ccgf_status autotune_plan(ccgf_handle *h, SigmaPlan *P, int pi, bool tensor_cores, typename cvec<R>::T *scr,
+                          typename cvec<R>::T *yout, cudaStream_t st) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    for (SigmaStep &s : P->steps) {
+        if (s.kind != STEP_GEMM || s.choice[pi] != 0) continue;
+        const GemmDesc &g = s.g;
+        TuneKey key{pi, s.a_buf, g.M, g.N, g.K, g.nred, g.batch, s.rowA_pos >= 0 ? 1 : 0,
+                    g.rsA, g.csA, g.rsB, g.csB, g.rsC, g.csC, g.beta.x != 0.0 || g.beta.y != 0.0};
+        {
+            std::lock_guard<std::mutex> lk(g_tuned_mu);
+            auto it = g_tuned.find(key);
+            if (it != g_tuned.end()) {
+                s.choice[pi] = it->second;
+                continue;
+            }
+        }
+        if (!e0) {
+            CCGF_CUDA_TRY(cudaEventCreate(&e0));
+            CCGF_CUDA_TRY(cudaEventCreate(&e1));
+        }
+        std::vector<int> cand;
+        for (int t = 1; t <= zgemm_tile_count(); ++t) cand.push_back(t);
+        if (sizeof(R) == 4 && tensor_cores && tc_zgemm_supported(g)) {
+            cand.push_back(CHOICE_TC_REG);
+            if (s.rowA_pos >= 0) cand.push_back(CHOICE_TC_TMA);
+        }
+        int best = 0;
+        float best_ms = 1e30f;
+        for (int c : cand) {
+            int n = run_gemm_step<R>(h, P, s, c, tensor_cores, scr, yout, st);
+            if (n == 0) continue;
+            h->launches += n;
+            float ms = 1e30f;
+            for (int rep = 0; rep < 2; ++rep) {
+                CCGF_CUDA_TRY(cudaEventRecord(e0, st));
+                h->launches += run_gemm_step<R>(h, P, s, c, tensor_cores, scr, yout, st);
+                CCGF_CUDA_TRY(cudaEventRecord(e1, st));
+                CCGF_CUDA_TRY(cudaEventSynchronize(e1));
+                float t = 0.f;
+                CCGF_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+                ms = t < ms ? t : ms;
+            }
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+        s.choice[pi] = best;
+        std::lock_guard<std::mutex> lk(g_tuned_mu);
+        g_tuned[key] = best;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return CCGF_OK;
+}
+
 template <typename R>
 void run_plan(ccgf_handle *h, SigmaPlan *P, const double2 *x, double2 *y, cudaStream_t st, T_arena<R> arena = nullptr,
               bool tensor_cores = false) {
     typedef typename cvec<R>::T T;
     const bool f64 = sizeof(R) == 8;
+    const int pi = f64 ? 0 : (tensor_cores ? 2 : 1);
     T *scr = arena ? arena : (f64 ? (T *)h->scratch.p : (T *)h->scratch_f.p);
     const i64 D = P->sector == CCGF_SECTOR_IP ? h->dim_ip : h->dim_ea;
     const i64 n = D * P->nv;
@@ -609,18 +744,7 @@ void run_plan(ccgf_handle *h, SigmaPlan *P, const double2 *x, double2 *y, cudaSt
         ++si;
         T *C = s.c_buf == BUF_Y ? yout : scr;
         if (s.kind == STEP_GEMM) {
-            GemmDesc d = s.g;
-            d.offA = offs + s.offA_pos;
-            d.offB = offs + s.offB_pos;
-            d.offC = offs + s.offC_pos;
-            const T *A = f64 ? (const T *)h->W[s.a_buf].p : (const T *)h->Wf[s.a_buf].p;
-            if constexpr (sizeof(R) == 4) {
-                if (tensor_cores && tc_zgemm_supported(d)) {
-                    h->launches += launch_tc_zgemm(d, A, scr, C, h->tc_err.p, st);
-                    continue;
-                }
-            }
-            h->launches += launch_zgemm<R>(d, A, scr, C, st, scr + P->seg[SEG_SPLITK], P->seg[SEG_END] - P->seg[SEG_SPLITK]);
+            h->launches += run_gemm_step<R>(h, P, s, s.choice[pi], tensor_cores, scr, yout, st);
         } else if (s.kind == STEP_PERM) {
             PermDesc d = s.p;
             d.offA = offs + s.offA_pos;
@@ -736,6 +860,14 @@ const char *plan_step_name(const ccgf_handle *h, int sector, int K, int step) {
     return P->steps[step].name;
 }
 
+void set_autotune(bool on) { g_autotune.store(on ? 1 : 0); }
+int plan_step_choice(const ccgf_handle *h, int sector, int K, int step, int pi) {
+    const SigmaPlan *P = plan_of(h, sector, K);
+    if (!P || step < 0 || step >= (int)P->steps.size() || pi < 0 || pi > 2) return -1;
+    const SigmaStep &s = P->steps[step];
+    return s.kind == STEP_GEMM ? s.choice[pi] : -1;
+}
+
 void free_plans(ccgf_handle *h) {
     for (SigmaPlan *p : h->plans)
         if (p) {
@@ -775,6 +907,7 @@ ccgf_status sigma_apply(ccgf_handle *h, int sector, int K, int nv, const double2
             dfree(h->scratch);
             CCGF_TRY(dalloc(h->scratch, P->scratch_elems));
         }
+        if (autotune_enabled()) CCGF_TRY(autotune_plan<double>(h, P, 0, false, (double2 *)h->scratch.p, y, st));
         run_plan<double>(h, P, x, y, st);
     } else {
         if (h->scratch_f.n < P->scratch_elems || h->yf.n < D * nv) {
@@ -794,6 +927,8 @@ ccgf_status sigma_apply(ccgf_handle *h, int sector, int K, int nv, const double2
             CCGF_TRY(dalloc(h->tc_err, 1));
             CCGF_CUDA_TRY(cudaMemset(h->tc_err.p, 0, sizeof(int)));
         }
+        if (tc) CCGF_TRY(tc_prepare(h, st));
+        if (autotune_enabled()) CCGF_TRY(autotune_plan<float>(h, P, tc ? 2 : 1, tc, h->scratch_f.p, h->yf.p, st));
         run_plan<float>(h, P, x, y, st, nullptr, tc);
     }
     CCGF_CUDA_TRY(cudaGetLastError());

@@ -20,7 +20,10 @@
 // the CTA records an error flag, stops issuing, waits (bounded) for its committed MMAs, frees its
 // TMEM and returns without writing C.
 #include "ccgf_internal.h"
+#include <cuda.h>
 #include <cstdint>
+#include <map>
+#include <mutex>
 
 namespace {
 
@@ -278,6 +281,283 @@ void launch_cols(dim3 grid, size_t smem, cudaStream_t st, const GemmDesc &d, con
     tc_zgemm_kernel<NCOLS><<<grid, NTHREADS, smem, st>>>(d, A, B, C, BNc, err);
 }
 
+
+// ----------------------------------------------------------------------------- TMA-fed variant
+// The A operand (an intermediate: fixed for the handle's lifetime) is pre-split once into TF32
+// hi / lo copies with A's own layout; TMA loads 128-row x 32-float boxes of both into shared memory
+// with the 128-byte swizzle (the canonical SW128 K-major layout of the MMA descriptor). Roles:
+//   warps 0-3  stage B' hi / lo from registers (as above), then run the epilogue (TMEM lane quarter = warp)
+//   warp 4     lane 0 issues the TMA loads of A
+//   warp 5     allocates TMEM; lane 0 issues the MMAs and commits them
+// Barriers per stage: fullA (TMA bytes), fullB (4 warp arrivals), empty (MMA commit); one more
+// barrier signals the finished accumulator to the epilogue.
+constexpr int TMA_THREADS = 192;
+constexpr int MAX_STAGES = 4;
+
+__device__ __forceinline__ uint64_t make_desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)1 << 16;             // leading byte offset: unused for swizzled K-major
+    d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;             // 128-byte swizzle
+    return d;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+// bounded wait that also gives up as soon as another role has aborted the CTA
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, unsigned parity, volatile int *abort_flag) {
+    const uint32_t a = smem_u32(bar);
+    const unsigned long long t0 = globaltimer_ns();
+    for (unsigned it = 0; it < (1u << 30); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 255) == 255 && (*abort_flag || globaltimer_ns() - t0 > kWaitLimitNs)) return false;
+    }
+    return false;
+}
+
+template <int NCOLS>
+__global__ void __launch_bounds__(TMA_THREADS, 1)
+    tc_zgemm_tma_kernel(GemmDesc d, const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
+                        const i64 *__restrict__ rowA, const float2 *__restrict__ B, float2 *__restrict__ C, int BNc, int S,
+                        int *err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte aligned base (the 128-byte swizzle pattern repeats every 8 rows = 1024 B)
+    unsigned char *base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+    const int NR = 2 * BNc;
+    const uint32_t a_bytes = BM * 2 * BKC * 4;   // 16 KB per part
+    const uint32_t b_bytes = (uint32_t)NR * 2 * BKC * 4;
+    const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
+    uint64_t *fullA = (uint64_t *)(base + S * stage_bytes);
+    uint64_t *fullB = fullA + MAX_STAGES;
+    uint64_t *empty = fullB + MAX_STAGES;
+    uint64_t *accum = empty + MAX_STAGES;
+    uint32_t *tmem_slot = (uint32_t *)(accum + 1);
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int b = blockIdx.z;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BNc;
+    const int ktiles = (d.K + BKC - 1) / BKC;
+    const int total = d.nred * ktiles;
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&fullA[s], 1);
+            mbar_init(&fullB[s], 4);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accum, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 5) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)), "r"(NCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    volatile int *abort_v = &abort_flag;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            // A producer
+            int issued = 0;
+            for (int kt = 0; kt < total; ++kt) {
+                const int s = kt % S;
+                if (kt >= S && !mbar_wait_or_abort(&empty[s], ((kt / S) - 1) & 1, abort_v)) {
+                    atomicExch(err, 1);
+                    *abort_v = 1;
+                    break;
+                }
+                const int r = kt / ktiles, k0 = (kt % ktiles) * BKC;
+                const int y = (int)rowA[(i64)b * d.nred + r] + m0;
+                unsigned char *sA = base + s * stage_bytes;
+                mbar_expect_tx(&fullA[s], 2 * a_bytes);
+                tma_load_2d(smem_u32(sA), &map_hi, 2 * k0, y, &fullA[s]);
+                tma_load_2d(smem_u32(sA + a_bytes), &map_lo, 2 * k0, y, &fullA[s]);
+                issued = kt + 1;
+            }
+            // no copy may still be writing shared memory when the CTA exits
+            for (int kt = issued - S > 0 ? issued - S : 0; kt < issued; ++kt)
+                if (!mbar_wait(&fullA[kt % S], (kt / S) & 1)) atomicExch(err, 1);
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {
+            // MMA issuer
+            const uint32_t idesc = make_idesc(NR);
+            int issued = 0;
+            for (int kt = 0; kt < total; ++kt) {
+                const int s = kt % S;
+                const unsigned par = (kt / S) & 1;
+                if (!mbar_wait_or_abort(&fullA[s], par, abort_v) || !mbar_wait_or_abort(&fullB[s], par, abort_v)) {
+                    atomicExch(err, 1);
+                    *abort_v = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                unsigned char *sA = base + s * stage_bytes;
+                const uint32_t aH = smem_u32(sA), aL = aH + a_bytes, bH = aL + a_bytes, bL = bH + b_bytes;
+#pragma unroll
+                for (int ks = 0; ks < (2 * BKC) / 8; ++ks) {
+                    const uint64_t dah = make_desc_sw128(aH + ks * 32), dal = make_desc_sw128(aL + ks * 32);
+                    const uint64_t dbh = make_desc(bH + ks * 256), dbl = make_desc(bL + ks * 256);
+                    mma_tf32(tmem, dah, dbh, idesc, (kt > 0 || ks > 0) ? 1u : 0u);
+                    mma_tf32(tmem, dah, dbl, idesc, 1u);
+                    mma_tf32(tmem, dal, dbh, idesc, 1u);
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&empty[s]))
+                             : "memory");
+                issued = kt + 1;
+            }
+            // the accumulator barrier fires when every MMA issued above has completed
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(accum))
+                         : "memory");
+            if (issued < total) *abort_v = 1;
+        }
+    } else {
+        // B' producers (warps 0-3), then the epilogue
+        const int nl = lane & 3, kp = lane >> 2;
+        for (int kt = 0; kt < total; ++kt) {
+            const int s = kt % S;
+            if (kt >= S && !mbar_wait_or_abort(&empty[s], ((kt / S) - 1) & 1, abort_v)) {
+                atomicExch(err, 1);
+                *abort_v = 1;
+                break;
+            }
+            const int r = kt / ktiles, k0 = (kt % ktiles) * BKC;
+            const float2 *Bb = B + d.offB[(i64)b * d.nred + r];
+            unsigned char *sBh = base + s * stage_bytes + 2 * a_bytes, *sBl = sBh + b_bytes;
+            const int k = k0 + kp * 2;
+            for (int t0 = warp; t0 < BNc / 4; t0 += 32) {
+                // up to 8 tasks per warp: all loads first, then the split and the stores
+                float2 v0[8], v1[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int t = t0 + 4 * q;
+                    v0[q] = make_float2(0.f, 0.f);
+                    v1[q] = v0[q];
+                    const int n = n0 + t * 4 + nl;
+                    if (t < BNc / 4 && n < d.N) {
+                        const float2 *col = Bb + (i64)n * d.csB;
+                        if (k < d.K) v0[q] = col[(i64)k * d.rsB];
+                        if (k + 1 < d.K) v1[q] = col[(i64)(k + 1) * d.rsB];
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int t = t0 + 4 * q;
+                    if (t >= BNc / 4) break;
+                    float rh0, rl0, ih0, il0, rh1, rl1, ih1, il1;
+                    split(v0[q].x, rh0, rl0);
+                    split(v0[q].y, ih0, il0);
+                    split(v1[q].x, rh1, rl1);
+                    split(v1[q].y, ih1, il1);
+                    const uint32_t o_re = t * 1024 + kp * 128 + (2 * nl) * 16, o_im = o_re + 16;
+                    if (kp & 1) {
+                        st_shared4(sBh + o_im, ih0, rh0, ih1, rh1);
+                        st_shared4(sBh + o_re, rh0, -ih0, rh1, -ih1);
+                        st_shared4(sBl + o_im, il0, rl0, il1, rl1);
+                        st_shared4(sBl + o_re, rl0, -il0, rl1, -il1);
+                    } else {
+                        st_shared4(sBh + o_re, rh0, -ih0, rh1, -ih1);
+                        st_shared4(sBh + o_im, ih0, rh0, ih1, rh1);
+                        st_shared4(sBl + o_re, rl0, -il0, rl1, -il1);
+                        st_shared4(sBl + o_im, il0, rl0, il1, rl1);
+                    }
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&fullB[s]);
+        }
+        // epilogue: wait for the accumulator, then TMEM -> registers -> C
+        const bool ok = mbar_wait_or_abort(accum, 0, abort_v);
+        if (!ok) atomicExch(err, 1);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (__all_sync(0xffffffffu, ok && !*abort_v)) {
+            const int m = m0 + warp * 32 + lane;
+            const float ax = (float)d.alpha.x, ay = (float)d.alpha.y, bx = (float)d.beta.x, by = (float)d.beta.y;
+            const bool use_beta = (d.beta.x != 0.0 || d.beta.y != 0.0);
+            float2 *Cb = C + d.offC[b];
+            for (int c0 = 0; c0 < NR; c0 += 8) {
+                uint32_t v[8];
+                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                             : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (m < d.M) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int n = n0 + (c0 >> 1) + q;
+                        if (n >= d.N) continue;
+                        const float re = __uint_as_float(v[2 * q]), im = __uint_as_float(v[2 * q + 1]);
+                        float2 *cp = Cb + (i64)m * d.rsC + (i64)n * d.csC;
+                        float2 o;
+                        o.x = ax * re - ay * im;
+                        o.y = ax * im + ay * re;
+                        if (use_beta) {
+                            const float2 cv = *cp;
+                            o.x += bx * cv.x - by * cv.y;
+                            o.y += bx * cv.y + by * cv.x;
+                        }
+                        *cp = o;
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 5) {
+        // every MMA this CTA issued has completed once the accumulator barrier fired; after an
+        // abort, wait for it (bounded) before the columns are released
+        if (*abort_v) {
+            if (!mbar_wait(accum, 0)) atomicExch(err, 1);
+            __syncwarp();
+        }
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
+    }
+}
+
+__global__ void tf32_split_kernel(const float2 *__restrict__ a, float2 *__restrict__ hi, float2 *__restrict__ lo, i64 n) {
+    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
+        const float2 v = a[i];
+        float hx, lx, hy, ly;
+        split(v.x, hx, lx);
+        split(v.y, hy, ly);
+        hi[i] = make_float2(hx, hy);
+        lo[i] = make_float2(lx, ly);
+    }
+}
+
+template <int NCOLS>
+void launch_tma_cols(dim3 grid, size_t smem, cudaStream_t st, const GemmDesc &d, const CUtensorMap &mh, const CUtensorMap &ml,
+                     const i64 *rowA, const float2 *B, float2 *C, int BNc, int S, int *err) {
+    cudaFuncSetAttribute(tc_zgemm_tma_kernel<NCOLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    tc_zgemm_tma_kernel<NCOLS><<<grid, TMA_THREADS, smem, st>>>(d, mh, ml, rowA, B, C, BNc, S, err);
+}
+
 }  // namespace
 
 bool tc_zgemm_supported(const GemmDesc &d) {
@@ -304,5 +584,115 @@ int launch_tc_zgemm(const GemmDesc &d, const float2 *A, const float2 *B, float2 
         launch_cols<128>(grid, smem, st, d, A, B, C, BNc, err);
     else
         launch_cols<256>(grid, smem, st, d, A, B, C, BNc, err);
+    return 1;
+}
+
+// ----------------------------------------------------------------------------- host side of the TMA path
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *, const cuuint64_t *,
+                                  const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+struct TcOperands {
+    DBuf<float2> hi[NBUF], lo[NBUF];
+    std::map<std::pair<int, i64>, std::pair<CUtensorMap, CUtensorMap>> maps;   // (buffer, row length) -> hi, lo
+};
+
+static EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    });
+    return fn;
+}
+
+ccgf_status tc_prepare(ccgf_handle *h, cudaStream_t st) {
+    if (h->tc_ops) return CCGF_OK;
+    TcOperands *T = new TcOperands();
+    for (int b = BUF_FOO; b < NBUF; ++b) {
+        if (!h->Wf[b].p) continue;
+        ccgf_status s = dalloc(T->hi[b], h->Wf[b].n);
+        if (s == CCGF_OK) s = dalloc(T->lo[b], h->Wf[b].n);
+        if (s != CCGF_OK) {
+            for (int c = 0; c < NBUF; ++c) { dfree(T->hi[c]); dfree(T->lo[c]); }
+            delete T;
+            return s;
+        }
+        const i64 n = h->Wf[b].n;
+        i64 g = ceil_div(n, 256);
+        tf32_split_kernel<<<(unsigned)(g > 152 * 16 ? 152 * 16 : g), 256, 0, st>>>(h->Wf[b].p, T->hi[b].p, T->lo[b].p, n);
+        h->launches++;
+    }
+    h->tc_ops = T;
+    CCGF_CUDA_TRY(cudaGetLastError());
+    return CCGF_OK;
+}
+
+void tc_free(ccgf_handle *h) {
+    TcOperands *T = (TcOperands *)h->tc_ops;
+    if (!T) return;
+    for (int c = 0; c < NBUF; ++c) {
+        dfree(T->hi[c]);
+        dfree(T->lo[c]);
+    }
+    delete T;
+    h->tc_ops = nullptr;
+}
+
+// tensor maps over the hi / lo copies of buffer a_buf viewed as rows of 2 rsA floats
+static bool tc_maps(ccgf_handle *h, int a_buf, i64 rsA, const CUtensorMap **mh, const CUtensorMap **ml) {
+    TcOperands *T = (TcOperands *)h->tc_ops;
+    if (!T || a_buf < BUF_FOO || a_buf >= NBUF || !T->hi[a_buf].p || rsA <= 0 || (rsA & 1)) return false;
+    auto key = std::make_pair(a_buf, rsA);
+    auto it = T->maps.find(key);
+    if (it == T->maps.end()) {
+        EncodeTiledFn enc = encode_fn();
+        if (!enc) return false;
+        const i64 rows = T->hi[a_buf].n / rsA;
+        if (rows < 1 || rows > (1LL << 31) - 1) return false;
+        cuuint64_t dims[2] = {(cuuint64_t)(2 * rsA), (cuuint64_t)rows};
+        cuuint64_t strides[1] = {(cuuint64_t)(2 * rsA * sizeof(float))};
+        cuuint32_t box[2] = {(cuuint32_t)(2 * BKC), (cuuint32_t)BM};
+        cuuint32_t estr[2] = {1, 1};
+        std::pair<CUtensorMap, CUtensorMap> m;
+        CUresult r1 = enc(&m.first, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)T->hi[a_buf].p, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        CUresult r2 = enc(&m.second, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)T->lo[a_buf].p, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS) return false;
+        it = T->maps.emplace(key, m).first;
+    }
+    *mh = &it->second.first;
+    *ml = &it->second.second;
+    return true;
+}
+
+int launch_tc_zgemm_tma(ccgf_handle *h, int a_buf, const GemmDesc &d, const i64 *rowA, const float2 *B, float2 *C, int *err,
+                        cudaStream_t st) {
+    const CUtensorMap *mh, *ml;
+    if (d.csA != 1 || !rowA || !tc_maps(h, a_buf, d.rsA, &mh, &ml)) return 0;
+    const int BNc = d.N >= 128 ? 128 : (int)ceil_div(d.N, 8) * 8;
+    const int NR = 2 * BNc;
+    const size_t stage = (size_t)2 * BM * 2 * BKC * 4 + (size_t)2 * NR * 2 * BKC * 4;
+    const size_t extra = 1024 + 8 * (3 * MAX_STAGES + 1) + 16;
+    int S = (int)((227 * 1024 - extra - 1024) / stage);   // 1024: static shared memory of the kernel
+    if (S > MAX_STAGES) S = MAX_STAGES;
+    if (S < 2) return 0;
+    const size_t smem = S * stage + extra;
+    const dim3 grid((unsigned)ceil_div(d.N, BNc), (unsigned)ceil_div(d.M, BM), (unsigned)d.batch);
+    if (NR <= 32)
+        launch_tma_cols<32>(grid, smem, st, d, *mh, *ml, rowA, B, C, BNc, S, err);
+    else if (NR <= 64)
+        launch_tma_cols<64>(grid, smem, st, d, *mh, *ml, rowA, B, C, BNc, S, err);
+    else if (NR <= 128)
+        launch_tma_cols<128>(grid, smem, st, d, *mh, *ml, rowA, B, C, BNc, S, err);
+    else
+        launch_tma_cols<256>(grid, smem, st, d, *mh, *ml, rowA, B, C, BNc, S, err);
     return 1;
 }

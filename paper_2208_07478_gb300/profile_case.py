@@ -3,8 +3,9 @@
     python -m paper_2208_07478_gb300.profile_case --kmesh 2 2 2 --nocc 4 --nvir 16 --sector ea --prec fp64
 
 Builds the similarity-transformed Hamiltonian blocks, then applies the EA (or
-IP) sigma of momentum 0 to nvec random vectors once (after one warm-up call
-that builds the plan). Prints the per-step device times of a profiled call.
+IP) sigma of momentum 0 to nvec random vectors (after one warm-up call that
+builds and tunes the plan), once more inside the NVTX range "profiled", and
+prints the per-step device times and kernel choices of a profiled call.
 """
 import argparse
 import os
@@ -42,9 +43,14 @@ def main():
     for _ in range(a.calls):
         fn(h, 0, x, y, prec=prec)
     torch.cuda.synchronize()
+    # one call inside an NVTX range, for captures restricted to it (ncu --nvtx --nvtx-include "profiled/")
+    torch.cuda.nvtx.range_push("profiled")
+    fn(h, 0, x, y, prec=prec)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     prof = B.sigma_profile(h, B.EA if a.sector == "ea" else B.IP, 0, x, y, prec=prec)
-    for name, ms, fl in prof:
-        print(f"{name:20s} {ms:9.3f} ms  {fl / 1e9:10.3f} GFLOP  {fl / max(ms, 1e-9) / 1e9:8.3f} TFLOP/s")
+    for name, ms, fl, kern in prof:
+        print(f"{name:20s} {ms:9.3f} ms  {fl / 1e9:10.3f} GFLOP  {fl / max(ms, 1e-9) / 1e9:8.3f} TFLOP/s  kernel {kern}")
     h.close()
 
 

@@ -7,7 +7,8 @@ sampled ones (k = 0 and k = 5, HOMO and LUMO, both sectors) by its own GMRES to
 rel. residual 1e-12 and contracts them with its own left vectors; each gives a
 full row (IP) or column (EA) of G_pq(k, w), compared element-wise with the GPU:
   plain FP64 form at tol 1e-12:        |dG| <= 1e-8
-  chosen form (FP32 sigma + FP64 refinement) at tol 1e-10: |dG| <= 1e-6 max(1, |G|)
+  chosen form (FP32 SIMT or 3xTF32 tensor-core sigma + FP64 refinement) at tol 1e-10:
+                                       |dG| <= 1e-6 max(1, |G|)
 and at the bench's tol 1e-6 the FP64-recomputed residual of every right-hand side is
 reported by the solver and must be <= 1e-6.
 """
@@ -93,15 +94,16 @@ def test_fullsize_plain_fp64(system, reference):
     assert err <= 1e-8, (err, gmax)
 
 
-def test_fullsize_chosen_form(system, reference):
+@pytest.mark.parametrize("prec", [B.FP32, B.TF32X3])
+def test_fullsize_chosen_form(system, reference, prec):
     s, ke, h = system
     om, ref = reference
-    err, gmax = compare(s, gpu_sectors(s, h, om, B.FP32, 1e-10), ref)
+    err, gmax = compare(s, gpu_sectors(s, h, om, prec, 1e-10), ref)
     assert err <= 1e-6 * max(1.0, gmax), (err, gmax)
 
 
 def test_fullsize_bench_tolerance_residuals(system):
     """At the benchmark's tol 1e-6 both forms report FP64 true residuals <= 1e-6 for every right-hand side."""
     s, ke, h = system
-    for prec in (B.FP64, B.FP32):
+    for prec in (B.FP64, B.FP32, B.TF32X3):
         gpu_sectors(s, h, s.omega[W_INDEX], prec, 1e-6)

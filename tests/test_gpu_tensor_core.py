@@ -22,20 +22,24 @@ from oracle.kccsd import KEOM
 from test_gpu_parity import oracle_gf
 
 
-@pytest.fixture(scope="module")
-def medium():
+@pytest.fixture(scope="module", params=["tuned", "defaults"])
+def medium(request):
+    """The medium system, with the measured kernel choice (autotuner) on, and off (defaults:
+    the tensor cores wherever the shape allows)."""
+    B.set_autotune(request.param == "tuned")
     s = make_system((2, 1, 1), 4, 12, 16, seed=11, L_sigma=0.06, t1_sigma=0.01, nomega=2,
                     omega_range=(-0.6, 0.6), eta=0.02)
     h = B.build_intermediates(s.kmesh, s.nocc, s.nvir, s.naux, s.mo_energy, s.L, s.t1, s.t2)
     ke = KEOM(s.kmesh, s.nocc, s.mo_energy, s.t1, s.t2, L=s.L)
-    yield s, h, ke
+    yield s, h, ke, request.param
     h.close()
+    B.set_autotune(True)
 
 
 @pytest.mark.parametrize("sector", ["ip", "ea"])
 @pytest.mark.parametrize("nvec", [1, 13])
 def test_tensor_core_sigma_matches_oracle(medium, sector, nvec):
-    s, h, ke = medium
+    s, h, ke, mode = medium
     d = h.dims()
     D = d["dim_ip"] if sector == "ip" else d["dim_ea"]
     rng = np.random.default_rng(17 + nvec)
@@ -52,15 +56,20 @@ def test_tensor_core_sigma_matches_oracle(medium, sector, nvec):
         err_tc = np.abs(y_tc.cpu().numpy() - ref).max() / scale
         err_32 = np.abs(y_32.cpu().numpy() - ref).max() / scale
         assert err_tc <= 3e-5, (K, err_tc, err_32)
-        if nvec > 1:
-            # with 13 columns the ring and ladder GEMMs reach the tensor cores: a different
+        if nvec > 1 and mode == "defaults":
+            # with 13 columns the ring and ladder GEMMs take the tensor cores: a different
             # arithmetic path from the SIMT FP32 kernels (with one column the IP GEMMs are too
             # narrow and every contraction stays on the SIMT path)
             assert not torch.equal(y_tc, y_32)
+        if mode == "tuned":
+            # every contraction of the plan has a measured choice: a SIMT tile or a tensor-core kernel
+            prof = B.sigma_profile(h, B.IP if sector == "ip" else B.EA, K, xd, y_tc, prec=B.TF32X3)
+            kern = [k for _, _, _, k in prof if k != -1]
+            assert kern and all(1 <= k <= 8 or k in (B.KERNEL_TC_TMA, B.KERNEL_TC_REG) for k in kern), kern
 
 
 def test_tensor_core_refined_greens_function(medium):
-    s, h, ke = medium
+    s, h, ke, mode = medium
     G = np.zeros((s.nk, len(s.omega), s.nmo, s.nmo), dtype=np.complex128)
     opt = B.default_options(prec=B.TF32X3, tol=1e-10, restart_m=30, max_iter=5000, max_refine=50)
     status, stats = B.solve_gf(h, B.BOTH, s.omega, s.eta, G, options=opt)
