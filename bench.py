@@ -46,6 +46,16 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 TF32_NOMINAL_RATIO = 1.1 / 2.25
 
 
+KERNEL_NAMES = {100: "tc_zgemm_tma_kernel", 101: "tc_zgemm_kernel", 102: "tc_zgemm_bulk_kernel"}
+
+
+def kernel_name(code, dtype):
+    """Name of the kernel behind a plan step's choice code (ccgf_sigma_step_kernel)."""
+    if code in KERNEL_NAMES:
+        return KERNEL_NAMES[code]
+    return f"zgemm_kernel<{dtype}>" + (f" tile #{code}" if code > 0 else "")
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -233,7 +243,7 @@ def gpu_arm(args):
     sig_fl = sum(p[2] for p in prof)
     top = max(prof, key=lambda p: p[1])
     achieved = top[2] / (top[1] / 1e3) / 1e12
-    roof = {"bound": "alu", "kernel": f"zgemm_kernel<double> ({top[0]})", "achieved": round(achieved, 4),
+    roof = {"bound": "alu", "kernel": f"{kernel_name(top[3], 'double')} ({top[0]})", "achieved": round(achieved, 4),
             "peak": round(FP64_PEAK_TFLOPS, 4), "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4),
             "traffic": None, "launch_ms": round(top[1], 4),
             "algorithmic_flops_per_launch": top[2],
@@ -299,7 +309,7 @@ def gpu_arm(args):
             ach = top32[2] / (top32[1] / 1e3) / 1e12
             cf["form"] = ("tensor-core sigma (tcgen05 kind::tf32, operands split hi+lo, 3 MMAs, FP32 accumulate) "
                           "inside FP64 refinement (FP64 Krylov basis, FP64 true residual)")
-            cf["roofline"] = {"bound": "tensor", "kernel": f"tc_zgemm_kernel ({top32[0]})", "achieved": round(ach, 3),
+            cf["roofline"] = {"bound": "tensor", "kernel": f"{kernel_name(top32[3], 'float')} ({top32[0]})", "achieved": round(ach, 3),
                               "peak": round(peak, 1), "unit": "TFLOP/s", "frac": round(ach / peak, 4),
                               "launch_ms": round(top32[1], 4), "algorithmic_flops_per_launch": top32[2],
                               "peak_basis": basis}

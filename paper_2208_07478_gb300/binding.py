@@ -215,7 +215,7 @@ def set_autotune(enable: bool):
     load().ccgf_set_autotune(1 if enable else 0)
 
 
-KERNEL_TC_TMA, KERNEL_TC_REG = 100, 101
+KERNEL_TC_TMA, KERNEL_TC_REG, KERNEL_TC_BULK = 100, 101, 102
 
 
 def sigma_ip_noalloc(h: Handle, kshift, x, y, stream=None):

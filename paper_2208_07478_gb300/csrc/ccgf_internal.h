@@ -86,6 +86,10 @@ struct ccgf_handle;
 // buffer does not qualify, else the number of launches.
 int launch_tc_zgemm_tma(ccgf_handle *h, int a_buf, const GemmDesc &d, const i64 *rowA, const float2 *B, float2 *C, int *err,
                         cudaStream_t st);
+// Bulk-fed variant: both operands by asynchronous copies; B' is first expanded into an image for
+// the nslots distinct B blocks (bsrc[slot] = offset, bslot[b * nred + r] = slot).
+int launch_tc_zgemm_bulk(ccgf_handle *h, int a_buf, const GemmDesc &d, const i64 *rowA, const i64 *bslot, const i64 *bsrc,
+                         int nslots, const float2 *B, float2 *C, int *err, cudaStream_t st);
 template <typename R>
 int launch_zpermute(const PermDesc &d, const typename cvec<R>::T *A, typename cvec<R>::T *C, cudaStream_t st);
 
@@ -115,6 +119,8 @@ struct SigmaStep {
     i64 offA_pos, offB_pos, offC_pos;   // positions in the plan's offset table
     i64 lad_rp, lad_rm;                 // ladder gather / scatter: scratch offsets of R+ / S+ and R- / S-
     i64 rowA_pos;                       // GEMM: position of offA / rsA per (batch, reduction), -1 if not integral
+    i64 bslot_pos, bsrc_pos;            // GEMM: slot of each (batch, reduction) B block, offsets of the distinct blocks
+    int nslots;                         // number of distinct B blocks
     int choice[3];                      // GEMM kernel measured per precision (0 = not tuned; see sigma.cu)
 };
 struct SigmaPlan {

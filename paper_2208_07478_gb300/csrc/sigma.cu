@@ -69,6 +69,22 @@ struct PlanBuilder {
             }
             if (rows.size() == oA.size()) s.rowA_pos = push(rows);
         }
+        // distinct B blocks (slots) for the bulk-fed tensor-core path
+        {
+            std::map<i64, i64> slot_of;
+            std::vector<i64> slots, src;
+            for (i64 b : oB) {
+                auto it = slot_of.find(b);
+                if (it == slot_of.end()) {
+                    it = slot_of.emplace(b, (i64)src.size()).first;
+                    src.push_back(b);
+                }
+                slots.push_back(it->second);
+            }
+            s.nslots = (int)src.size();
+            s.bslot_pos = push(slots);
+            s.bsrc_pos = push(src);
+        }
         P->steps.push_back(s);
     }
     // dims (outer..inner), source strides (scratch), destination strides
@@ -605,10 +621,10 @@ inline unsigned gsz(i64 n) {
     return (unsigned)(g > 152 * 32 ? 152 * 32 : (g > 0 ? g : 1));
 }
 
-// GEMM kernel choices of a plan step: 0 = default (tensor cores through TMA when the operand
-// qualifies, else the register-fed tensor-core kernel; SIMT tile by the launcher's model),
-// k in 1..zgemm_tile_count() = SIMT kernel with the launcher's k-th tile, or one of these two
-enum { CHOICE_TC_TMA = 100, CHOICE_TC_REG = 101 };
+// GEMM kernel choices of a plan step: 0 = default (the bulk-fed tensor-core kernel when the A
+// operand is TMA-addressable, else the register-fed one; SIMT tile by the launcher's model),
+// k in 1..zgemm_tile_count() = SIMT kernel with the launcher's k-th tile, or one of these three
+enum { CHOICE_TC_TMA = 100, CHOICE_TC_REG = 101, CHOICE_TC_BULK = 102 };
 
 // one GEMM step with the given choice; returns the number of launches (0: choice not applicable)
 template <typename R>
@@ -626,9 +642,12 @@ int run_gemm_step(ccgf_handle *h, const SigmaPlan *P, const SigmaStep &s, int ch
     if constexpr (sizeof(R) == 4) {
         if (tensor_cores && tc_zgemm_supported(d) && (choice == 0 || choice >= CHOICE_TC_TMA)) {
             int n = 0;
-            if ((choice == 0 || choice == CHOICE_TC_TMA) && s.rowA_pos >= 0)
+            if ((choice == 0 || choice == CHOICE_TC_BULK) && s.rowA_pos >= 0)
+                n = launch_tc_zgemm_bulk(h, s.a_buf, d, offs + s.rowA_pos, offs + s.bslot_pos, offs + s.bsrc_pos, s.nslots, scr, C,
+                                         h->tc_err.p, st);
+            if (n == 0 && choice == CHOICE_TC_TMA && s.rowA_pos >= 0)
                 n = launch_tc_zgemm_tma(h, s.a_buf, d, offs + s.rowA_pos, scr, C, h->tc_err.p, st);
-            if (n == 0 && choice != CHOICE_TC_TMA) n = launch_tc_zgemm(d, A, scr, C, h->tc_err.p, st);
+            if (n == 0 && (choice == 0 || choice == CHOICE_TC_REG)) n = launch_tc_zgemm(d, A, scr, C, h->tc_err.p, st);
             return n;
         }
     }
@@ -692,7 +711,10 @@ ccgf_status autotune_plan(ccgf_handle *h, SigmaPlan *P, int pi, bool tensor_core
         for (int t = 1; t <= zgemm_tile_count(); ++t) cand.push_back(t);
         if (sizeof(R) == 4 && tensor_cores && tc_zgemm_supported(g)) {
             cand.push_back(CHOICE_TC_REG);
-            if (s.rowA_pos >= 0) cand.push_back(CHOICE_TC_TMA);
+            if (s.rowA_pos >= 0) {
+                cand.push_back(CHOICE_TC_TMA);
+                cand.push_back(CHOICE_TC_BULK);
+            }
         }
         int best = 0;
         float best_ms = 1e30f;

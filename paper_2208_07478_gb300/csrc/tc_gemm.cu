@@ -24,6 +24,7 @@
 #include <cstdint>
 #include <map>
 #include <mutex>
+#include <tuple>
 
 namespace {
 
@@ -558,6 +559,236 @@ void launch_tma_cols(dim3 grid, size_t smem, cudaStream_t st, const GemmDesc &d,
     tc_zgemm_tma_kernel<NCOLS><<<grid, TMA_THREADS, smem, st>>>(d, mh, ml, rowA, B, C, BNc, S, err);
 }
 
+
+// ----------------------------------------------------------------------------- bulk-fed variant
+// Both operands arrive by asynchronous copies, so no thread stages data in the main loop:
+//  - A by TMA (64-byte swizzle, 128 rows x 16 floats = 8 complex K per stage) from the TF32
+//    hi / lo copies;
+//  - B' from an image written just before by bimage_kernel: for every distinct B block (slot),
+//    N tile and K tile, the TF32 hi then lo parts of the 2x2-embedded tile in the canonical
+//    no-swizzle K-major layout (8-row groups 512 B apart, core matrices 128 B apart along K),
+//    fetched with one cp.async.bulk per stage.
+// Warp 0 lane 0 produces, warp 1 allocates TMEM and its lane 0 issues the MMAs, warps 2-5 run
+// the epilogue (TMEM lane quarter = warp % 4). Up to 8 stages of 16 real K each.
+constexpr int BKC3 = 8;                  // complex K per stage
+constexpr int MAX_STAGES3 = 8;
+
+__host__ __device__ constexpr int tc3_bn(int N) { return N >= 128 ? 128 : ((N + 7) / 8) * 8; }
+
+__device__ __forceinline__ uint64_t make_desc_sw64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)1 << 16;             // leading byte offset: unused for swizzled K-major
+    d |= (uint64_t)(512 >> 4) << 32;    // stride byte offset: 8 rows x 64 B
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;             // 64-byte swizzle
+    return d;
+}
+__device__ __forceinline__ uint64_t make_desc_k16(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)(128 >> 4) << 16;    // next core matrix along K
+    d |= (uint64_t)(512 >> 4) << 32;    // next 8-row group
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"((uint64_t)src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// B' image of the slots: thread = (slot, N tile, K tile, 4-column group t, k pair kp, column nl);
+// writes rows 2n and 2n+1 (16 bytes each) of the hi part and of the lo part
+__global__ void bimage_kernel(GemmDesc d, const float2 *__restrict__ B, const i64 *__restrict__ bsrc, int nslots, int BNc,
+                              int ntiles, int ktiles, float *__restrict__ img) {
+    const int NR = 2 * BNc;
+    const i64 chunk = (i64)NR * 2 * (2 * BKC3);   // floats per (slot, N tile, K tile): hi + lo
+    const i64 per_tile = (i64)(BNc / 4) * 16;       // threads per (slot, N tile, K tile)
+    const i64 total = (i64)nslots * ntiles * ktiles * per_tile;
+    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (i64)gridDim.x * blockDim.x) {
+        const int nl = (int)(i & 3), kp = (int)((i >> 2) & 3);
+        i64 r = i >> 4;
+        const int t = (int)(r % (BNc / 4));
+        r /= (BNc / 4);
+        const int kt = (int)(r % ktiles);
+        r /= ktiles;
+        const int nt = (int)(r % ntiles);
+        const int slot = (int)(r / ntiles);
+        const int n = nt * BNc + t * 4 + nl, k = kt * BKC3 + kp * 2;
+        float2 v0 = make_float2(0.f, 0.f), v1 = v0;
+        if (n < d.N) {
+            const float2 *col = B + bsrc[slot] + (i64)n * d.csB;
+            if (k < d.K) v0 = col[(i64)k * d.rsB];
+            if (k + 1 < d.K) v1 = col[(i64)(k + 1) * d.rsB];
+        }
+        float rh0, rl0, ih0, il0, rh1, rl1, ih1, il1;
+        split(v0.x, rh0, rl0);
+        split(v0.y, ih0, il0);
+        split(v1.x, rh1, rl1);
+        split(v1.y, ih1, il1);
+        float *hi = img + (((i64)slot * ntiles + nt) * ktiles + kt) * chunk;
+        float *lo = hi + (i64)NR * (2 * BKC3);
+        const int o_re = t * 128 + kp * 32 + nl * 8, o_im = o_re + 4;   // in floats: row 2n, row 2n+1
+        *(float4 *)(hi + o_re) = make_float4(rh0, -ih0, rh1, -ih1);
+        *(float4 *)(hi + o_im) = make_float4(ih0, rh0, ih1, rh1);
+        *(float4 *)(lo + o_re) = make_float4(rl0, -il0, rl1, -il1);
+        *(float4 *)(lo + o_im) = make_float4(il0, rl0, il1, rl1);
+    }
+}
+
+template <int NCOLS>
+__global__ void __launch_bounds__(TMA_THREADS, 1)
+    tc_zgemm_bulk_kernel(GemmDesc d, const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
+                         const i64 *__restrict__ rowA, const i64 *__restrict__ bslot, const float *__restrict__ img,
+                         float2 *__restrict__ C, int BNc, int S, int *err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+    const int NR = 2 * BNc;
+    const uint32_t a_bytes = BM * 2 * BKC3 * 4;                  // 8 KB per part
+    const uint32_t b_bytes = (uint32_t)NR * 2 * (2 * BKC3) * 4;  // hi + lo
+    const uint32_t stage_bytes = 2 * a_bytes + b_bytes;
+    uint64_t *full = (uint64_t *)(base + S * stage_bytes);
+    uint64_t *empty = full + MAX_STAGES3;
+    uint64_t *accum = empty + MAX_STAGES3;
+    uint32_t *tmem_slot = (uint32_t *)(accum + 1);
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int b = blockIdx.z, nt = blockIdx.x;
+    const int m0 = blockIdx.y * BM, n0 = nt * BNc;
+    const int ktiles = (d.K + BKC3 - 1) / BKC3;
+    const int ntiles = gridDim.x;
+    const int total = d.nred * ktiles;
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accum, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)), "r"(NCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    volatile int *abort_v = &abort_flag;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int kt = 0; kt < total; ++kt) {
+                const int s = kt % S;
+                if (kt >= S && !mbar_wait_or_abort(&empty[s], ((kt / S) - 1) & 1, abort_v)) {
+                    atomicExch(err, 1);
+                    *abort_v = 1;
+                    break;
+                }
+                const int r = kt / ktiles, kk = kt % ktiles;
+                const i64 br = (i64)b * d.nred + r;
+                const int y = (int)rowA[br] + m0;
+                unsigned char *sA = base + s * stage_bytes;
+                const float *src = img + (((i64)bslot[br] * ntiles + nt) * ktiles + kk) * ((i64)b_bytes / 4);
+                mbar_expect_tx(&full[s], 2 * a_bytes + b_bytes);
+                tma_load_2d(smem_u32(sA), &map_hi, 2 * kk * BKC3, y, &full[s]);
+                tma_load_2d(smem_u32(sA + a_bytes), &map_lo, 2 * kk * BKC3, y, &full[s]);
+                bulk_load(smem_u32(sA + 2 * a_bytes), src, b_bytes, &full[s]);
+                issued = kt + 1;
+            }
+            for (int kt = issued - S > 0 ? issued - S : 0; kt < issued; ++kt)
+                if (!mbar_wait(&full[kt % S], (kt / S) & 1)) atomicExch(err, 1);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = make_idesc(NR);
+            int issued = 0;
+            for (int kt = 0; kt < total; ++kt) {
+                const int s = kt % S;
+                if (!mbar_wait_or_abort(&full[s], (kt / S) & 1, abort_v)) {
+                    atomicExch(err, 1);
+                    *abort_v = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t aH = smem_u32(base + s * stage_bytes), aL = aH + a_bytes, bH = aL + a_bytes, bL = bH + b_bytes / 2;
+#pragma unroll
+                for (int ks = 0; ks < (2 * BKC3) / 8; ++ks) {
+                    const uint64_t dah = make_desc_sw64(aH + ks * 32), dal = make_desc_sw64(aL + ks * 32);
+                    const uint64_t dbh = make_desc_k16(bH + ks * 256), dbl = make_desc_k16(bL + ks * 256);
+                    mma_tf32(tmem, dah, dbh, idesc, (kt > 0 || ks > 0) ? 1u : 0u);
+                    mma_tf32(tmem, dah, dbl, idesc, 1u);
+                    mma_tf32(tmem, dal, dbh, idesc, 1u);
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&empty[s]))
+                             : "memory");
+                issued = kt + 1;
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(accum))
+                         : "memory");
+            if (issued < total) *abort_v = 1;
+        }
+    } else {
+        const int quarter = warp & 3;
+        const bool ok = mbar_wait_or_abort(accum, 0, abort_v);
+        if (!ok) atomicExch(err, 1);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (__all_sync(0xffffffffu, ok && !*abort_v)) {
+            const int m = m0 + quarter * 32 + lane;
+            const float ax = (float)d.alpha.x, ay = (float)d.alpha.y, bx = (float)d.beta.x, by = (float)d.beta.y;
+            const bool use_beta = (d.beta.x != 0.0 || d.beta.y != 0.0);
+            float2 *Cb = C + d.offC[b];
+            for (int c0 = 0; c0 < NR; c0 += 8) {
+                uint32_t v[8];
+                const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                             : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (m < d.M) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int n = n0 + (c0 >> 1) + q;
+                        if (n >= d.N) continue;
+                        const float re = __uint_as_float(v[2 * q]), im = __uint_as_float(v[2 * q + 1]);
+                        float2 *cp = Cb + (i64)m * d.rsC + (i64)n * d.csC;
+                        float2 o;
+                        o.x = ax * re - ay * im;
+                        o.y = ax * im + ay * re;
+                        if (use_beta) {
+                            const float2 cv = *cp;
+                            o.x += bx * cv.x - by * cv.y;
+                            o.y += bx * cv.y + by * cv.x;
+                        }
+                        *cp = o;
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1) {
+        if (*abort_v) {
+            if (!mbar_wait(accum, 0)) atomicExch(err, 1);
+            __syncwarp();
+        }
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
+    }
+}
+
+template <int NCOLS>
+void launch_bulk_cols(dim3 grid, size_t smem, cudaStream_t st, const GemmDesc &d, const CUtensorMap &mh, const CUtensorMap &ml,
+                      const i64 *rowA, const i64 *bslot, const float *img, float2 *C, int BNc, int S, int *err) {
+    cudaFuncSetAttribute(tc_zgemm_bulk_kernel<NCOLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    tc_zgemm_bulk_kernel<NCOLS><<<grid, TMA_THREADS, smem, st>>>(d, mh, ml, rowA, bslot, img, C, BNc, S, err);
+}
+
 }  // namespace
 
 bool tc_zgemm_supported(const GemmDesc &d) {
@@ -594,7 +825,9 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
 
 struct TcOperands {
     DBuf<float2> hi[NBUF], lo[NBUF];
-    std::map<std::pair<int, i64>, std::pair<CUtensorMap, CUtensorMap>> maps;   // (buffer, row length) -> hi, lo
+    // (buffer, row length, box floats) -> hi, lo maps (box 32: 128-byte swizzle, 16: 64-byte swizzle)
+    std::map<std::tuple<int, i64, int>, std::pair<CUtensorMap, CUtensorMap>> maps;
+    DBuf<float> img;   // B' images of the bulk-fed kernel (grown on demand)
 };
 
 static EncodeTiledFn encode_fn() {
@@ -639,15 +872,16 @@ void tc_free(ccgf_handle *h) {
         dfree(T->hi[c]);
         dfree(T->lo[c]);
     }
+    dfree(T->img);
     delete T;
     h->tc_ops = nullptr;
 }
 
 // tensor maps over the hi / lo copies of buffer a_buf viewed as rows of 2 rsA floats
-static bool tc_maps(ccgf_handle *h, int a_buf, i64 rsA, const CUtensorMap **mh, const CUtensorMap **ml) {
+static bool tc_maps(ccgf_handle *h, int a_buf, i64 rsA, int box_floats, const CUtensorMap **mh, const CUtensorMap **ml) {
     TcOperands *T = (TcOperands *)h->tc_ops;
     if (!T || a_buf < BUF_FOO || a_buf >= NBUF || !T->hi[a_buf].p || rsA <= 0 || (rsA & 1)) return false;
-    auto key = std::make_pair(a_buf, rsA);
+    auto key = std::make_tuple(a_buf, rsA, box_floats);
     auto it = T->maps.find(key);
     if (it == T->maps.end()) {
         EncodeTiledFn enc = encode_fn();
@@ -656,15 +890,14 @@ static bool tc_maps(ccgf_handle *h, int a_buf, i64 rsA, const CUtensorMap **mh, 
         if (rows < 1 || rows > (1LL << 31) - 1) return false;
         cuuint64_t dims[2] = {(cuuint64_t)(2 * rsA), (cuuint64_t)rows};
         cuuint64_t strides[1] = {(cuuint64_t)(2 * rsA * sizeof(float))};
-        cuuint32_t box[2] = {(cuuint32_t)(2 * BKC), (cuuint32_t)BM};
+        cuuint32_t box[2] = {(cuuint32_t)box_floats, (cuuint32_t)BM};
         cuuint32_t estr[2] = {1, 1};
+        const CUtensorMapSwizzle sw = box_floats == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
         std::pair<CUtensorMap, CUtensorMap> m;
         CUresult r1 = enc(&m.first, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)T->hi[a_buf].p, dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         CUresult r2 = enc(&m.second, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)T->lo[a_buf].p, dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS) return false;
         it = T->maps.emplace(key, m).first;
     }
@@ -676,7 +909,7 @@ static bool tc_maps(ccgf_handle *h, int a_buf, i64 rsA, const CUtensorMap **mh, 
 int launch_tc_zgemm_tma(ccgf_handle *h, int a_buf, const GemmDesc &d, const i64 *rowA, const float2 *B, float2 *C, int *err,
                         cudaStream_t st) {
     const CUtensorMap *mh, *ml;
-    if (d.csA != 1 || !rowA || !tc_maps(h, a_buf, d.rsA, &mh, &ml)) return 0;
+    if (d.csA != 1 || !rowA || !tc_maps(h, a_buf, d.rsA, 2 * BKC, &mh, &ml)) return 0;
     const int BNc = d.N >= 128 ? 128 : (int)ceil_div(d.N, 8) * 8;
     const int NR = 2 * BNc;
     const size_t stage = (size_t)2 * BM * 2 * BKC * 4 + (size_t)2 * NR * 2 * BKC * 4;
@@ -695,4 +928,44 @@ int launch_tc_zgemm_tma(ccgf_handle *h, int a_buf, const GemmDesc &d, const i64 
     else
         launch_tma_cols<256>(grid, smem, st, d, *mh, *ml, rowA, B, C, BNc, S, err);
     return 1;
+}
+
+// Bulk-fed variant: B' image for the nslots distinct B blocks (bsrc: their offsets; bslot: slot of
+// each (batch, reduction) entry, both device tables), then the GEMM. Returns the launch count, or
+// 0 when the operand does not qualify (nothing launched).
+int launch_tc_zgemm_bulk(ccgf_handle *h, int a_buf, const GemmDesc &d, const i64 *rowA, const i64 *bslot, const i64 *bsrc,
+                         int nslots, const float2 *B, float2 *C, int *err, cudaStream_t st) {
+    const CUtensorMap *mh, *ml;
+    TcOperands *T = (TcOperands *)h->tc_ops;
+    if (!T || d.csA != 1 || !rowA || !bslot || !bsrc || nslots < 1 || !tc_maps(h, a_buf, d.rsA, 2 * BKC3, &mh, &ml)) return 0;
+    const int BNc = tc3_bn(d.N), NR = 2 * BNc;
+    const int ntiles = (int)ceil_div(d.N, BNc), ktiles = (int)ceil_div(d.K, BKC3);
+    const i64 img_floats = (i64)nslots * ntiles * ktiles * NR * 2 * (2 * BKC3);
+    if (T->img.n < img_floats) {
+        // grow the image buffer (synchronises: the previous image may still be in use)
+        if (cudaStreamSynchronize(st) != cudaSuccess) return 0;
+        dfree(T->img);
+        if (dalloc(T->img, img_floats) != CCGF_OK) return 0;
+    }
+    const size_t stage = (size_t)2 * BM * 2 * BKC3 * 4 + (size_t)NR * 2 * (2 * BKC3) * 4;
+    const size_t extra = 1024 + 8 * (2 * MAX_STAGES3 + 1) + 16;
+    int S = (int)((227 * 1024 - extra - 1024) / stage);
+    if (S > MAX_STAGES3) S = MAX_STAGES3;
+    if (S < 2) return 0;
+    const size_t smem = S * stage + extra;
+    {
+        const i64 total = (i64)nslots * ntiles * ktiles * (BNc / 4) * 16;
+        i64 g = ceil_div(total, 256);
+        bimage_kernel<<<(unsigned)(g > 152 * 32 ? 152 * 32 : g), 256, 0, st>>>(d, B, bsrc, nslots, BNc, ntiles, ktiles, T->img.p);
+    }
+    const dim3 grid((unsigned)ntiles, (unsigned)ceil_div(d.M, BM), (unsigned)d.batch);
+    if (NR <= 32)
+        launch_bulk_cols<32>(grid, smem, st, d, *mh, *ml, rowA, bslot, T->img.p, C, BNc, S, err);
+    else if (NR <= 64)
+        launch_bulk_cols<64>(grid, smem, st, d, *mh, *ml, rowA, bslot, T->img.p, C, BNc, S, err);
+    else if (NR <= 128)
+        launch_bulk_cols<128>(grid, smem, st, d, *mh, *ml, rowA, bslot, T->img.p, C, BNc, S, err);
+    else
+        launch_bulk_cols<256>(grid, smem, st, d, *mh, *ml, rowA, bslot, T->img.p, C, BNc, S, err);
+    return 2;
 }
