@@ -217,6 +217,13 @@ void ccgf_set_autotune(int enable);
  * with both operands by asynchronous copies (B from a pre-expanded image). */
 int ccgf_sigma_step_kernel(const ccgf_handle *h, int sector, int kshift, int step, ccgf_precision prec);
 
+/* Self-test of the bounded device waits (no counterpart in the paper): one warp allocates
+ * tensor memory, waits on an mbarrier that nothing arrives on for limit_ms (0 < limit_ms <= 2000),
+ * records the timeout, frees the tensor memory and returns. Returns CCGF_ERR_TIMEOUT when the
+ * wait gave up as designed (the CUDA context stays usable), CCGF_OK if it did not. Synchronises
+ * the stream. */
+ccgf_status ccgf_tensor_wait_selftest(double limit_ms, void *stream);
+
 /* Number of kernels this handle has launched since it was built (build included). */
 long long ccgf_launch_count(const ccgf_handle *h);
 

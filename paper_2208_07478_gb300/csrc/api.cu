@@ -230,6 +230,25 @@ const char *ccgf_sigma_step_name(const ccgf_handle *h, int sector, int kshift, i
 long long ccgf_launch_count(const ccgf_handle *h) { return h ? h->launches : 0; }
 
 void ccgf_set_autotune(int enable) { set_autotune(enable != 0); }
+
+ccgf_status ccgf_tensor_wait_selftest(double limit_ms, void *stream) {
+    if (!(limit_ms > 0.0) || limit_ms > 2000.0) { set_last_error("limit_ms must be in (0, 2000]"); return CCGF_ERR_INVALID_ARG; }
+    cudaStream_t st = (cudaStream_t)stream;
+    DBuf<int> flag;
+    CCGF_TRY(dalloc(flag, 1));
+    CCGF_CUDA_TRY(cudaMemsetAsync(flag.p, 0, sizeof(int), st));
+    launch_wait_selftest(limit_ms, flag.p, st);
+    int v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, flag.p, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dfree(flag);
+    if (e != cudaSuccess) { set_last_error(cudaGetErrorString(e)); return CCGF_ERR_CUDA; }
+    if (v) {
+        set_last_error("tensor-core wait self-test: the wait gave up after its limit, as designed");
+        return CCGF_ERR_TIMEOUT;
+    }
+    return CCGF_OK;
+}
 int ccgf_sigma_step_kernel(const ccgf_handle *h, int sector, int kshift, int step, ccgf_precision prec) {
     if (!h || (int)prec < 0 || (int)prec > 2) return -1;
     return plan_step_choice(h, sector, kshift, step, (int)prec);

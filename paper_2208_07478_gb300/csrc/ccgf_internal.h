@@ -189,6 +189,8 @@ void set_autotune(bool on);
 int plan_step_choice(const ccgf_handle *h, int sector, int K, int step, int prec_index);
 // reads and clears the tensor-core error flag (synchronises st); CCGF_ERR_TIMEOUT when it was set
 ccgf_status tc_error_check(ccgf_handle *h, cudaStream_t st);
+// tc_gemm.cu: the bounded-wait timeout path alone (one warp, a barrier nothing arrives on)
+void launch_wait_selftest(double limit_ms, int *err, cudaStream_t st);
 // tc_gemm.cu: TF32 hi / lo copies of every FP32 intermediate, freed by tc_free
 ccgf_status tc_prepare(ccgf_handle *h, cudaStream_t st);
 void tc_free(ccgf_handle *h);

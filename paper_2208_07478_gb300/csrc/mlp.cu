@@ -9,7 +9,10 @@
 // (the neighbours carried to w along the element's own diagonal resolvent):
 //   eta x- / |b_p|, eta x+ / |b_p|, eta base / |b_p| (re, im each), t, (w+ - w-) / (10 eta),
 //   eta g(w), eta g(w-), eta g(w+) (re, im each)                                  -> F = 14.
-// Output: the correction eta (x0 - base) / |b_p| (re, im); the last layer starts at zero, so an
+// Output: the correction eta (x0 - base) / |b_p| (re, im) divided by (span / (10 eta))^2, span =
+// w+ - w-: the error of an interpolation between neighbours grows with the square of their
+// spacing, so this scaling carries what is learned on training triples (neighbours two grid
+// steps apart) to inference between adjacent points. The last layer starts at zero, so an
 // untrained network predicts the baseline. Network: tanh(f W1 + b1) -> tanh(. W2 + b2) -> . W3 + b3,
 // hidden 256; FP32 master weights, forward with bfloat16-rounded weight matrices, FP32
 // accumulation. Training: Adam on the mean squared error against converged solutions at
@@ -300,12 +303,12 @@ __global__ void features_kernel(FeatArgs a, float *Fm, double2 *Base) {
     }
 }
 // x0[mu][c] = base + (y0 + i y1) |b_p| / eta for rows of the chunk starting at element mu0
-__global__ void apply_kernel(const float *Y, const double2 *Base, const double *bnorm, double eta, i64 mu0, i64 nmu, int nv,
-                             int nw, double2 *X, double2 *Xbase) {
+__global__ void apply_kernel(const float *Y, const double2 *Base, const double *bnorm, const double *span2, double eta, i64 mu0,
+                             i64 nmu, int nv, int nw, double2 *X, double2 *Xbase) {
     const i64 rows = nmu * nv;
     for (i64 r = (i64)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (i64)gridDim.x * blockDim.x) {
         const int c = r % nv, p = c / nw;
-        const double sc = bnorm[p] / eta;
+        const double sc = bnorm[p] / eta * span2[c % nw];
         X[mu0 * nv + r] = make_double2(Base[r].x + sc * Y[2 * r], Base[r].y + sc * Y[2 * r + 1]);
         if (Xbase) Xbase[mu0 * nv + r] = Base[r];
     }
@@ -342,7 +345,8 @@ __global__ void train_rows_mixed_kernel(FeatArgs a, int nk, int n, const double2
         double2 base;
         feat_row(b, mu, p, 0, Fm + r * kF, &base);
         const double2 x = b.store[((i64)i * a.D + mu) * a.N + p];
-        const double sc = a.eta / (b.bnorm[p] > 0 ? b.bnorm[p] : 1.0);
+        const double sf = (a.tom[ih] - a.tom[il]) / (10.0 * a.eta);
+        const double sc = a.eta / (b.bnorm[p] > 0 ? b.bnorm[p] : 1.0) / (sf * sf);
         T[2 * r] = (float)(sc * (x.x - base.x));
         T[2 * r + 1] = (float)(sc * (x.y - base.y));
     }
@@ -473,14 +477,22 @@ ccgf_status warmstart_infer(ccgf_handle *h, int sector, int K, const double *om,
     const int nv = N * nw;
     std::vector<int> lo, hi;
     neighbours(w->omega, om, nw, lo, hi);
+    // (span / (10 eta))^2 per column frequency: the scale of the learned correction
+    std::vector<double> span2(nw);
+    for (int j = 0; j < nw; ++j) {
+        const double sf = (w->omega[hi[j]] - w->omega[lo[j]]) / (10.0 * w->eta);
+        span2[j] = sf * sf;
+    }
     DBuf<int> dlo, dhi;
-    DBuf<double> dom;
+    DBuf<double> dom, dspan2;
     CCGF_TRY(dalloc(dlo, nw));
     CCGF_TRY(dalloc(dhi, nw));
     CCGF_TRY(dalloc(dom, nw));
+    CCGF_TRY(dalloc(dspan2, nw));
     CCGF_CUDA_TRY(cudaMemcpyAsync(dlo.p, lo.data(), sizeof(int) * nw, cudaMemcpyHostToDevice, st));
     CCGF_CUDA_TRY(cudaMemcpyAsync(dhi.p, hi.data(), sizeof(int) * nw, cudaMemcpyHostToDevice, st));
     CCGF_CUDA_TRY(cudaMemcpyAsync(dom.p, om, sizeof(double) * nw, cudaMemcpyHostToDevice, st));
+    CCGF_CUDA_TRY(cudaMemcpyAsync(dspan2.p, span2.data(), sizeof(double) * nw, cudaMemcpyHostToDevice, st));
     FeatArgs a{};
     a.D = D;
     a.N = N;
@@ -498,7 +510,7 @@ ccgf_status warmstart_infer(ccgf_handle *h, int sector, int K, const double *om,
     h->launches += round_params(w->th.p, w->thr.p, w->F, w->H, w->bf16, st);
     const i64 mu_chunk = std::max<i64>(1, (i64)(1 << 19) / nv);
     ccgf_status s = ensure_rows(w, mu_chunk * nv);
-    if (s != CCGF_OK) { dfree(dlo); dfree(dhi); dfree(dom); return s; }
+    if (s != CCGF_OK) { dfree(dlo); dfree(dhi); dfree(dom); dfree(dspan2); return s; }
     for (i64 mu0 = 0; mu0 < D; mu0 += mu_chunk) {
         a.mu0 = mu0;
         a.nmu = std::min(mu_chunk, D - mu0);
@@ -508,7 +520,7 @@ ccgf_status warmstart_infer(ccgf_handle *h, int sector, int K, const double *om,
         h->launches += 2 + forward(w->thr.p, w->F, w->H, rows, w->Fm.p, w->H1.p, w->H2.p, w->Y.p, st);
         scale_kernel<<<gsz(rows * 2), 256, 0, st>>>(w->Y.p, rows * 2, w->tscale);
         h->launches++;
-        apply_kernel<<<gsz(rows), 256, 0, st>>>(w->Y.p, w->Base.p, a.bnorm, w->eta, mu0, a.nmu, nv, nw, X,
+        apply_kernel<<<gsz(rows), 256, 0, st>>>(w->Y.p, w->Base.p, a.bnorm, dspan2.p, w->eta, mu0, a.nmu, nv, nw, X,
                                                 w->use_net ? Xbase : nullptr);
         h->launches++;
     }
@@ -517,6 +529,7 @@ ccgf_status warmstart_infer(ccgf_handle *h, int sector, int K, const double *om,
     dfree(dlo);
     dfree(dhi);
     dfree(dom);
+    dfree(dspan2);
     *used = true;
     *net = w->use_net;
     return CCGF_OK;

@@ -71,7 +71,7 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     return t;
 }
 // bounded wait for the completion of the phase with the given parity; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, unsigned long long limit_ns = kWaitLimitNs) {
     const uint32_t a = smem_u32(bar);
     const unsigned long long t0 = globaltimer_ns();
     for (unsigned it = 0; it < (1u << 30); ++it) {
@@ -82,7 +82,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
             : "r"(a), "r"(parity)
             : "memory");
         if (done) return true;
-        if ((it & 255) == 255 && globaltimer_ns() - t0 > kWaitLimitNs) return false;
+        if ((it & 255) == 255 && globaltimer_ns() - t0 > limit_ns) return false;
     }
     return false;
 }
@@ -789,6 +789,29 @@ void launch_bulk_cols(dim3 grid, size_t smem, cudaStream_t st, const GemmDesc &d
     tc_zgemm_bulk_kernel<NCOLS><<<grid, TMA_THREADS, smem, st>>>(d, mh, ml, rowA, bslot, img, C, BNc, S, err);
 }
 
+
+// The timeout path of the tensor-core kernels on its own: one warp allocates TMEM, waits on an
+// mbarrier that nothing arrives on with the given limit, records the timeout in *err, frees TMEM
+// and returns.
+__global__ void wait_selftest_kernel(unsigned long long limit_ns, int *err) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t slot;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&slot)), "r"(32));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = slot;
+    const bool ok = mbar_wait(&bar, 0, limit_ns);
+    if (!ok && threadIdx.x == 0) atomicExch(err, 1);
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32));
+}
+
 }  // namespace
 
 bool tc_zgemm_supported(const GemmDesc &d) {
@@ -968,4 +991,8 @@ int launch_tc_zgemm_bulk(ccgf_handle *h, int a_buf, const GemmDesc &d, const i64
     else
         launch_bulk_cols<256>(grid, smem, st, d, *mh, *ml, rowA, bslot, T->img.p, C, BNc, S, err);
     return 2;
+}
+
+void launch_wait_selftest(double limit_ms, int *err, cudaStream_t st) {
+    wait_selftest_kernel<<<1, 32, 0, st>>>((unsigned long long)(limit_ms * 1e6), err);
 }

@@ -78,3 +78,21 @@ def test_tensor_core_refined_greens_function(medium):
     assert stats["lowp_sigma_calls"] > 0
     Gref = oracle_gf(ke, s.omega, s.eta)
     assert np.abs(G - Gref).max() <= 1e-6 * max(1.0, np.abs(Gref).max())
+
+
+def test_bounded_wait_gives_up_and_context_survives(medium):
+    """The tensor-core kernels' wait path: a barrier nothing arrives on times out after its limit,
+    the status says so, and the next computation on the same context is still correct."""
+    import time
+    s, h, ke, mode = medium
+    t0 = time.perf_counter()
+    st = B.tensor_wait_selftest(50.0)
+    dt = time.perf_counter() - t0
+    assert st == B.CCGF_ERR_TIMEOUT
+    assert dt < 5.0
+    D = h.dims()["dim_ea"]
+    x = torch.from_numpy(np.random.default_rng(2).normal(size=(3, D)) + 0j).cuda()
+    y = torch.zeros_like(x)
+    B.sigma_ea(h, 0, x, y, prec=B.TF32X3)
+    ref = np.stack([ke.sigma_ea(0, x[c].cpu().numpy()) for c in range(3)])
+    assert np.abs(y.cpu().numpy() - ref).max() <= 3e-5 * np.abs(ref).max()

@@ -78,3 +78,13 @@ def test_trained_network_gain():
     cold, warm, loss, t = _held_out(400)
     assert np.isfinite(loss) and loss <= t["warm_val_loss_baseline"] + 1e-15
     assert warm["inner_iterations"] <= cold["inner_iterations"]
+
+
+def test_trained_network_vs_baseline():
+    """What the trained correction adds over the baseline alone on the held-out frequencies:
+    when validation keeps the network, its warm start needs no more GMRES iterations."""
+    _, base, _, _ = _held_out(0)
+    _, net, loss, t = _held_out(400)
+    print(f"held-out iterations: baseline {base['inner_iterations']}, trained network {net['inner_iterations']}")
+    if t["warm_val_loss"] < t["warm_val_loss_baseline"]:
+        assert net["inner_iterations"] <= base["inner_iterations"]
