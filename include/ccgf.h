@@ -101,6 +101,9 @@ typedef struct {
     long long warm_fallbacks;   /* right-hand sides where the cold start was kept         */
     double warm_val_loss;       /* ccgf_train_warmstart: validation loss of the network   */
     double warm_val_loss_baseline; /* ... of the baseline alone (zero correction)         */
+    double warm_rel_residual;   /* mean |b - M x0| / |b| of the starts used (cold = 1)     */
+    double warm_rel_residual_net;  /* ... of the network's prediction (0 when not used)   */
+    double warm_rel_residual_base; /* ... of the baseline alone                           */
 } ccgf_stats;
 
 typedef struct ccgf_handle ccgf_handle;

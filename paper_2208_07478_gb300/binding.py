@@ -38,7 +38,9 @@ class Stats(C.Structure):
                 ("fp64_sigma_calls", C.c_longlong), ("lowp_sigma_calls", C.c_longlong),
                 ("max_rel_residual", C.c_double), ("sigma_ms", C.c_double), ("total_ms", C.c_double),
                 ("kernel_launches", C.c_longlong), ("warm_columns", C.c_longlong), ("warm_fallbacks", C.c_longlong),
-                ("warm_val_loss", C.c_double), ("warm_val_loss_baseline", C.c_double)]
+                ("warm_val_loss", C.c_double), ("warm_val_loss_baseline", C.c_double),
+                ("warm_rel_residual", C.c_double), ("warm_rel_residual_net", C.c_double),
+                ("warm_rel_residual_base", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

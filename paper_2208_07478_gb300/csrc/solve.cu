@@ -331,6 +331,8 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
     const double tol = opt->tol;
     const i64 Gn = (i64)nk * nomega * N * N;
     ccgf_stats S{};
+    double warm_rel_sum = 0, warm_net_sum = 0, warm_base_sum = 0;
+    i64 warm_count = 0;
     cudaEvent_t ev0, ev1, es0, es1;
     cudaEventCreate(&ev0);
     cudaEventCreate(&ev1);
@@ -456,6 +458,16 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                             if (net && rb[c] < best) { best = rb[c]; mode[c] = 2; }
                             S.warm_columns += mode[c] ? 1 : 0;
                             S.warm_fallbacks += mode[c] ? 0 : 1;
+                            if (b2[c] > 0) {
+                                warm_rel_sum += std::sqrt(best / b2[c]);
+                                if (net) {
+                                    warm_net_sum += std::sqrt(rn[c] / b2[c]);
+                                    warm_base_sum += std::sqrt(rb[c] / b2[c]);
+                                } else {
+                                    warm_base_sum += std::sqrt(rn[c] / b2[c]);
+                                }
+                                warm_count++;
+                            }
                         }
                         CCGF_CUDA_TRY(cudaMemcpyAsync(active.p, mode.data(), sizeof(int) * nv, cudaMemcpyHostToDevice, st));
                         select_kernel<<<g1(Dn), 256, 0, st>>>(active.p, X.p, R.p, U.p, V.p, B.p, D, nv);
@@ -604,6 +616,11 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
     float tms = 0;
     cudaEventElapsedTime(&tms, ev0, ev1);
     S.total_ms = tms;
+    if (warm_count > 0) {
+        S.warm_rel_residual = warm_rel_sum / warm_count;
+        S.warm_rel_residual_net = warm_net_sum / warm_count;
+        S.warm_rel_residual_base = warm_base_sum / warm_count;
+    }
     S.sigma_ms = sigma_ms;
     S.kernel_launches = h->launches - launches0;
     if (stats) *stats = S;

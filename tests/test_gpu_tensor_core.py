@@ -68,6 +68,29 @@ def test_tensor_core_sigma_matches_oracle(medium, sector, nvec):
             assert kern and all(1 <= k <= 8 or k in (B.KERNEL_TC_TMA, B.KERNEL_TC_REG, B.KERNEL_TC_BULK) for k in kern), kern
 
 
+@pytest.mark.parametrize("o,v", [(3, 11), (2, 9)])
+def test_tensor_core_odd_sizes(o, v):
+    """Odd nvir: A rows of odd length are not TMA-addressable (fallback to the register-fed
+    kernel), ragged K tails in every contraction; defaults and tuned kernels both match."""
+    s = make_system((3, 1, 1), o, v, 10, seed=13, L_sigma=0.06, t1_sigma=0.01, nomega=0)
+    h = B.build_intermediates(s.kmesh, s.nocc, s.nvir, s.naux, s.mo_energy, s.L, s.t1, s.t2)
+    ke = KEOM(s.kmesh, s.nocc, s.mo_energy, s.t1, s.t2, L=s.L)
+    rng = np.random.default_rng(5)
+    try:
+        for sector in ("ip", "ea"):
+            D = h.dims()["dim_ip" if sector == "ip" else "dim_ea"]
+            fn = B.sigma_ip if sector == "ip" else B.sigma_ea
+            sig = ke.sigma_ip if sector == "ip" else ke.sigma_ea
+            for K in range(s.nk):
+                x = rng.normal(size=(9, D)) + 1j * rng.normal(size=(9, D))
+                y = torch.zeros((9, D), dtype=torch.complex128, device="cuda")
+                fn(h, K, torch.from_numpy(x).cuda(), y, prec=B.TF32X3)
+                ref = np.stack([sig(K, x[c]) for c in range(9)])
+                assert np.abs(y.cpu().numpy() - ref).max() <= 3e-5 * np.abs(ref).max(), (sector, K)
+    finally:
+        h.close()
+
+
 def test_tensor_core_refined_greens_function(medium):
     s, h, ke, mode = medium
     G = np.zeros((s.nk, len(s.omega), s.nmo, s.nmo), dtype=np.complex128)
