@@ -16,7 +16,7 @@
 // untrained network predicts the baseline. Network: tanh(f W1 + b1) -> tanh(. W2 + b2) -> . W3 + b3,
 // hidden 256; FP32 master weights, forward with bfloat16-rounded weight matrices, FP32
 // accumulation. Training: Adam on the mean squared error against converged solutions at
-// interior training frequencies (each one predicted from its two neighbours).
+// interior training frequencies (each one predicted from neighbours one or two grid steps away).
 #include "ccgf_internal.h"
 #include <cuda_bf16.h>
 #include <algorithm>
@@ -335,8 +335,11 @@ __global__ void train_rows_mixed_kernel(FeatArgs a, int nk, int n, const double2
         b.store = store_all + (i64)K * n * a.D * a.N;
         b.d = d_all + (i64)K * a.D;
         b.bnorm = bnorm_all + (i64)K * a.N;
-        // neighbours i - 1, i + 1 of training point i (w index 0 of per-row tables is not used)
-        const int il = i - 1, ih = i + 1;
+        // neighbours i - a, i + b of training point i, a, b in {1, 2} where the grid allows: varied
+        // positions t and spans (w index 0 of per-row tables is not used)
+        const unsigned h4 = hash32(h1 ^ 0xc2b2ae35u);
+        const int a_off = (i >= 2 && (h4 & 1)) ? 2 : 1, b_off = (i + 2 <= n - 1 && (h4 & 2)) ? 2 : 1;
+        const int il = i - a_off, ih = i + b_off;
         int lo_hi[2] = {il, ih};
         double om = a.tom[i];
         b.wlo = lo_hi;
