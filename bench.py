@@ -47,13 +47,18 @@ TF32_NOMINAL_RATIO = 1.1 / 2.25
 
 
 KERNEL_NAMES = {100: "tc_zgemm_tma_kernel", 101: "tc_zgemm_kernel", 102: "tc_zgemm_bulk_kernel"}
+# the SIMT launcher's per-thread tile candidates (rows, columns of complex outputs), in its order
+SIMT_TILES = [(4, 4), (3, 4), (2, 4), (4, 3), (4, 2), (4, 7), (3, 7), (2, 7)]
 
 
 def kernel_name(code, dtype):
     """Name of the kernel behind a plan step's choice code (ccgf_sigma_step_kernel)."""
     if code in KERNEL_NAMES:
         return KERNEL_NAMES[code]
-    return f"zgemm_kernel<{dtype}>" + (f" tile #{code}" if code > 0 else "")
+    if code <= 0:
+        return f"zgemm_kernel<{dtype}>"
+    tm, tn = SIMT_TILES[code % 1000 - 1]
+    return f"zgemm_kernel<{dtype}, {tm}, {tn}>" + (f" split-K {code // 1000}" if code >= 1000 else "")
 
 
 def measured_peaks():

@@ -39,6 +39,8 @@ void destroy(ccgf_handle *h) {
     dfree(h->scratch_f);
     dfree(h->yf);
     dfree(h->tc_err);
+    dfree(h->splitw64);
+    dfree(h->splitw32);
     tc_free(h);
     delete h;
 }

@@ -54,12 +54,15 @@ struct GemmDesc {
     const i64 *offA, *offB, *offC;   // device offset tables
     double2 alpha, beta;
     int tile;                        // SIMT per-thread tile: 0 = the launcher's model choice, k = its k-th candidate
+    int ksplit;                      // SIMT split of K across CTAs: 0 = the launcher's model choice
 };
 int zgemm_tile_count();              // number of SIMT tile candidates
 // Long-K GEMMs with few output tiles split K across CTAs (deterministic: partial sums go to
 // `work`, then one reduction applies alpha / beta); work may be NULL (no split).
 int zgemm_ksplit(const GemmDesc &d);
-i64 zgemm_workspace_elems(const GemmDesc &d);
+// split-K that fills whole waves of one CTA per SM for SIMT tile `tile` (1 = no split)
+int zgemm_wave_split(const GemmDesc &d, int tile);
+i64 zgemm_workspace_elems(const GemmDesc &d);   // split-K partials needed (0 without a split)
 // returns the number of kernels launched
 template <typename R>
 int launch_zgemm(const GemmDesc &d, const typename cvec<R>::T *A, const typename cvec<R>::T *B,
@@ -161,6 +164,9 @@ struct ccgf_handle {
     // scratch arena for sigma (FP64 and FP32 variants) and the FP32 output
     DBuf<double2> scratch;
     DBuf<float2> scratch_f, yf;
+    // split-K workspaces of the autotuner's wave-filling splits (grown on demand)
+    DBuf<double2> splitw64;
+    DBuf<float2> splitw32;
     // error flag of the tensor-core GEMMs and their TF32-split operands (made on first CCGF_TF32X3 use)
     DBuf<int> tc_err;
     void *tc_ops = nullptr;

@@ -213,6 +213,11 @@ static TileShape pick_shape(const GemmDesc &d) {
 }
 
 int zgemm_ksplit(const GemmDesc &d) {
+    if (d.ksplit > 0) {
+        // explicit split: at least 16 of K per slice
+        i64 kmax = ceil_div(d.K, 16);
+        return (int)(d.ksplit < kmax ? d.ksplit : kmax);
+    }
     // Enough CTAs to cover the SMs twice; every split keeps at least 8 k-tiles of work.
     const TileShape s = pick_shape(d);
     const i64 tiles = ceil_div(d.M, 16 * s.tm) * ceil_div(d.N, 16 * s.tn) * (i64)d.batch;
@@ -221,6 +226,22 @@ int zgemm_ksplit(const GemmDesc &d) {
     i64 kmax = d.K / 128;
     if (k > kmax) k = kmax;
     return (int)(k < 1 ? 1 : k);
+}
+// Split (2..8) that best fills whole waves of one CTA per SM for the given tile, keeping at least
+// 32 of K per slice; 1 when no split improves the wave efficiency by more than 5 %.
+int zgemm_wave_split(const GemmDesc &d, int tile) {
+    GemmDesc e = d;
+    e.tile = tile;
+    const TileShape s = pick_shape(e);
+    const double ctas = (double)ceil_div(d.M, 16 * s.tm) * ceil_div(d.N, 16 * s.tn) * d.batch;
+    auto eff = [&](int k) {
+        const double w = ctas * k / 152.0;
+        return w / std::ceil(w);
+    };
+    int best = 1;
+    for (int k = 2; k <= 8 && d.K / k >= 32; ++k)
+        if (eff(k) > eff(best) + 1e-12) best = k;
+    return eff(best) > 1.05 * eff(1) ? best : 1;
 }
 i64 zgemm_workspace_elems(const GemmDesc &d) {
     int s = zgemm_ksplit(d);

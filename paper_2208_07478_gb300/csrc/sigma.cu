@@ -124,7 +124,8 @@ void scratch_layout(const ccgf_handle *h, int nv, i64 seg[SEG_END + 1]) {
     const i64 nk2 = (i64)h->nk * h->nk, o = h->o, v = h->v;
     i64 dmax = h->dim_ip > h->dim_ea ? h->dim_ip : h->dim_ea;
     i64 r2max = nk2 * o * v * (o > v ? o : v);
-    // split-K partials: at most 304 slices of an (o+v) x nv product
+    // split-K partials of the launcher's own splits: at most 304 slices of an (o+v) x nv product
+    // (the autotuner's wave-filling splits use a separate workspace of the handle)
     i64 sizes[SEG_END] = {dmax * nv, r2max * nv, r2max * nv, r2max * nv, r2max * nv, r2max * nv, (o + v) * (i64)nv,
                           304 * (o + v) * (i64)nv};
     i64 pos = 0;
@@ -623,8 +624,9 @@ inline unsigned gsz(i64 n) {
 
 // GEMM kernel choices of a plan step: 0 = default (the bulk-fed tensor-core kernel when the A
 // operand is TMA-addressable, else the register-fed one; SIMT tile by the launcher's model),
-// k in 1..zgemm_tile_count() = SIMT kernel with the launcher's k-th tile, or one of these three
-enum { CHOICE_TC_TMA = 100, CHOICE_TC_REG = 101, CHOICE_TC_BULK = 102 };
+// k in 1..zgemm_tile_count() = SIMT kernel with the launcher's k-th tile, k + 1000 s = the same
+// with K split over s CTAs (s >= 2, partial sums reduced by a second kernel), or one of these three
+enum { CHOICE_TC_TMA = 100, CHOICE_TC_REG = 101, CHOICE_TC_BULK = 102, CHOICE_SPLIT = 1000 };
 
 // one GEMM step with the given choice; returns the number of launches (0: choice not applicable)
 template <typename R>
@@ -651,8 +653,15 @@ int run_gemm_step(ccgf_handle *h, const SigmaPlan *P, const SigmaStep &s, int ch
             return n;
         }
     }
-    if (choice >= CHOICE_TC_TMA) return 0;
-    d.tile = choice;
+    if (choice >= CHOICE_TC_TMA && choice < CHOICE_SPLIT) return 0;
+    d.tile = choice % CHOICE_SPLIT;
+    d.ksplit = choice / CHOICE_SPLIT;
+    if (d.ksplit > 1) {
+        // wave-filling split: partial sums in the handle's split workspace (sized by the autotuner;
+        // the launcher runs unsplit if it is too small)
+        if (f64) return launch_zgemm<R>(d, A, scr, C, st, (T *)h->splitw64.p, h->splitw64.n);
+        return launch_zgemm<R>(d, A, scr, C, st, (T *)h->splitw32.p, h->splitw32.n);
+    }
     return launch_zgemm<R>(d, A, scr, C, st, scr + P->seg[SEG_SPLITK], P->seg[SEG_END] - P->seg[SEG_SPLITK]);
 }
 
@@ -686,29 +695,58 @@ bool autotune_enabled() {
     return v != 0;
 }
 
+// grows the handle's split-K workspace of this precision to hold a `choice` split of GEMM g
+template <typename R> ccgf_status ensure_split_ws(ccgf_handle *h, const GemmDesc &g, int choice, cudaStream_t st) {
+    if (choice < CHOICE_SPLIT) return CCGF_OK;
+    GemmDesc d = g;
+    d.tile = choice % CHOICE_SPLIT;
+    d.ksplit = choice / CHOICE_SPLIT;
+    const i64 need = zgemm_workspace_elems(d);
+    const i64 cap = sizeof(R) == 8 ? h->splitw64.n : h->splitw32.n;
+    if (need <= cap) return CCGF_OK;
+    CCGF_CUDA_TRY(cudaStreamSynchronize(st));
+    if (sizeof(R) == 8) {
+        dfree(h->splitw64);
+        CCGF_TRY(dalloc(h->splitw64, need));
+    } else {
+        dfree(h->splitw32);
+        CCGF_TRY(dalloc(h->splitw32, need));
+    }
+    return CCGF_OK;
+}
+
 template <typename R>
 ccgf_status autotune_plan(ccgf_handle *h, SigmaPlan *P, int pi, bool tensor_cores, typename cvec<R>::T *scr,
                           typename cvec<R>::T *yout, cudaStream_t st) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     for (SigmaStep &s : P->steps) {
-        if (s.kind != STEP_GEMM || s.choice[pi] != 0) continue;
+        if (s.kind != STEP_GEMM) continue;
+        if (s.choice[pi] != 0) {
+            CCGF_TRY(ensure_split_ws<R>(h, s.g, s.choice[pi], st));
+            continue;
+        }
         const GemmDesc &g = s.g;
         TuneKey key{pi, s.a_buf, g.M, g.N, g.K, g.nred, g.batch, s.rowA_pos >= 0 ? 1 : 0,
                     g.rsA, g.csA, g.rsB, g.csB, g.rsC, g.csC, g.beta.x != 0.0 || g.beta.y != 0.0};
         {
             std::lock_guard<std::mutex> lk(g_tuned_mu);
             auto it = g_tuned.find(key);
-            if (it != g_tuned.end()) {
-                s.choice[pi] = it->second;
-                continue;
-            }
+            if (it != g_tuned.end()) s.choice[pi] = it->second;
+        }
+        if (s.choice[pi] != 0) {
+            CCGF_TRY(ensure_split_ws<R>(h, s.g, s.choice[pi], st));
+            continue;
         }
         if (!e0) {
             CCGF_CUDA_TRY(cudaEventCreate(&e0));
             CCGF_CUDA_TRY(cudaEventCreate(&e1));
         }
         std::vector<int> cand;
-        for (int t = 1; t <= zgemm_tile_count(); ++t) cand.push_back(t);
+        for (int t = 1; t <= zgemm_tile_count(); ++t) {
+            cand.push_back(t);
+            const int ks = zgemm_wave_split(g, t);
+            if (ks > 1) cand.push_back(t + CHOICE_SPLIT * ks);
+        }
         if (sizeof(R) == 4 && tensor_cores && tc_zgemm_supported(g)) {
             cand.push_back(CHOICE_TC_REG);
             if (s.rowA_pos >= 0) {
@@ -719,6 +757,7 @@ ccgf_status autotune_plan(ccgf_handle *h, SigmaPlan *P, int pi, bool tensor_core
         int best = 0;
         float best_ms = 1e30f;
         for (int c : cand) {
+            CCGF_TRY(ensure_split_ws<R>(h, s.g, c, st));
             int n = run_gemm_step<R>(h, P, s, c, tensor_cores, scr, yout, st);
             if (n == 0) continue;
             h->launches += n;
