@@ -75,13 +75,17 @@ __global__ void __launch_bounds__(256) zgemm_kernel(GemmDesc d, const typename c
     const bool use_beta = (d.beta.x != 0.0 || d.beta.y != 0.0);
     for (int bz = blockIdx.z; bz < d.batch * ksplit; bz += gridDim.z) {
         const int b = bz / ksplit, ks = bz % ksplit;
-        const int kbeg = ks * kchunk, kend = min(d.K, kbeg + kchunk);
+        // a split covers a K range of every momentum block (nred = 1), or whole momentum blocks
+        // [rbeg, rend) (nred > 1, kchunk = K; rchunk blocks per split)
+        const int rchunk = d.nred > 1 ? (d.nred + ksplit - 1) / ksplit : 1;
+        const int rbeg = d.nred > 1 ? ks * rchunk : 0, rend = d.nred > 1 ? min(d.nred, rbeg + rchunk) : 1;
+        const int kbeg = d.nred > 1 ? 0 : ks * kchunk, kend = d.nred > 1 ? d.K : min(d.K, kbeg + kchunk);
         T acc[TM][TN];
 #pragma unroll
         for (int i = 0; i < TM; ++i)
 #pragma unroll
             for (int j = 0; j < TN; ++j) acc[i][j] = cz<T>();
-        for (int r = 0; r < d.nred; ++r) {
+        for (int r = rbeg; r < rend; ++r) {
             const T *Ab = A + d.offA[(i64)b * d.nred + r];
             const T *Bb = B + d.offB[(i64)b * d.nred + r];
             for (int k0 = kbeg; k0 < kend; k0 += BK) {
@@ -214,7 +218,12 @@ static TileShape pick_shape(const GemmDesc &d) {
 
 int zgemm_ksplit(const GemmDesc &d) {
     if (d.ksplit > 0) {
-        // explicit split: at least 16 of K per slice
+        // explicit split: over the momentum blocks when there are several (every split non-empty),
+        // else over K with at least 16 per slice
+        if (d.nred > 1) {
+            const int rchunk = (int)ceil_div(d.nred, d.ksplit);
+            return (int)ceil_div(d.nred, rchunk);
+        }
         i64 kmax = ceil_div(d.K, 16);
         return (int)(d.ksplit < kmax ? d.ksplit : kmax);
     }
@@ -227,8 +236,9 @@ int zgemm_ksplit(const GemmDesc &d) {
     if (k > kmax) k = kmax;
     return (int)(k < 1 ? 1 : k);
 }
-// Split (2..8) that best fills whole waves of one CTA per SM for the given tile, keeping at least
-// 32 of K per slice; 1 when no split improves the wave efficiency by more than 5 %.
+// Split (2..8) that best fills whole waves of one CTA per SM for the given tile: over whole momentum
+// blocks when there are several (only splits that divide them evenly into non-empty groups), else
+// over K with at least 32 per slice; 1 when no split improves the wave efficiency by more than 5 %.
 int zgemm_wave_split(const GemmDesc &d, int tile) {
     GemmDesc e = d;
     e.tile = tile;
@@ -238,9 +248,17 @@ int zgemm_wave_split(const GemmDesc &d, int tile) {
         const double w = ctas * k / 152.0;
         return w / std::ceil(w);
     };
+    // effective number of splits: over momentum blocks (nred > 1) or over K (>= 32 per slice)
+    auto splits = [&](int k) -> int {
+        if (d.nred > 1) return (int)ceil_div(d.nred, ceil_div(d.nred, k));
+        return d.K / k >= 32 ? k : 0;
+    };
     int best = 1;
-    for (int k = 2; k <= 8 && d.K / k >= 32; ++k)
+    for (int k = 2; k <= 8; ++k) {
+        const int e = splits(k);
+        if (e < 2 || e != k) continue;
         if (eff(k) > eff(best) + 1e-12) best = k;
+    }
     return eff(best) > 1.05 * eff(1) ? best : 1;
 }
 i64 zgemm_workspace_elems(const GemmDesc &d) {
@@ -263,7 +281,7 @@ int launch_zgemm(const GemmDesc &d, const typename cvec<R>::T *A, const typename
     int ks = zgemm_ksplit(d);
     if (ks > 1 && (work == nullptr || work_elems < zgemm_workspace_elems(d))) ks = 1;
     int kchunk = d.K;
-    if (ks > 1) {
+    if (ks > 1 && d.nred == 1) {
         kchunk = (int)(ceil_div(ceil_div(d.K, ks), 16) * 16);
         ks = (int)ceil_div(d.K, kchunk);
     }

@@ -21,6 +21,8 @@
 // TMEM and returns without writing C.
 #include "ccgf_internal.h"
 #include <cuda.h>
+#include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <map>
 #include <mutex>
@@ -573,7 +575,30 @@ void launch_tma_cols(dim3 grid, size_t smem, cudaStream_t st, const GemmDesc &d,
 constexpr int BKC3 = 8;                  // complex K per stage
 constexpr int MAX_STAGES3 = 8;
 
-__host__ __device__ constexpr int tc3_bn(int N) { return N >= 128 ? 128 : ((N + 7) / 8) * 8; }
+// complex N tile of the bulk-fed kernel: N rounded up to 8 when it fits one tile; otherwise the
+// width in 64..128 (multiples of 8) with the least modelled time: padded work, divided by the wave
+// efficiency of one CTA per SM, times the shared-memory pressure of the tile (per MMA clock the
+// operand reads take 8192 / NR + 64 bytes and the copies landing in shared memory 5461 / NR + 43,
+// NR = 2 BN real columns, against 128 B/clk)
+static int tc3_bn(const GemmDesc &d) {
+    if (d.N <= 128) return (int)ceil_div(d.N, 8) * 8;
+    const double mt = (double)ceil_div(d.M, BM) * d.batch;
+    int best = 128;
+    double best_cost = 1e300;
+    for (int bn = 128; bn >= 64; bn -= 8) {
+        const double nt = (double)ceil_div(d.N, bn);
+        const double waves = nt * mt / 152.0;
+        const double eff = waves >= 1.0 ? waves / std::ceil(waves) : waves;
+        const double nr = 2.0 * bn;
+        const double smem = std::max(1.0, (8192.0 / nr + 64.0 + 5461.0 / nr + 42.7) / 128.0);
+        const double cost = nt * bn / eff * smem;
+        if (cost < best_cost * (1 - 1e-9)) {
+            best_cost = cost;
+            best = bn;
+        }
+    }
+    return best;
+}
 
 __device__ __forceinline__ uint64_t make_desc_sw64(uint32_t saddr) {
     uint64_t d = 0;
@@ -961,7 +986,7 @@ int launch_tc_zgemm_bulk(ccgf_handle *h, int a_buf, const GemmDesc &d, const i64
     const CUtensorMap *mh, *ml;
     TcOperands *T = (TcOperands *)h->tc_ops;
     if (!T || d.csA != 1 || !rowA || !bslot || !bsrc || nslots < 1 || !tc_maps(h, a_buf, d.rsA, 2 * BKC3, &mh, &ml)) return 0;
-    const int BNc = tc3_bn(d.N), NR = 2 * BNc;
+    const int BNc = tc3_bn(d), NR = 2 * BNc;
     const int ntiles = (int)ceil_div(d.N, BNc), ktiles = (int)ceil_div(d.K, BKC3);
     const i64 img_floats = (i64)nslots * ntiles * ktiles * NR * 2 * (2 * BKC3);
     if (T->img.n < img_floats) {
