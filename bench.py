@@ -48,7 +48,7 @@ TF32_NOMINAL_RATIO = 1.1 / 2.25
 
 KERNEL_NAMES = {100: "tc_zgemm_tma_kernel", 101: "tc_zgemm_kernel", 102: "tc_zgemm_bulk_kernel"}
 # the SIMT launcher's per-thread tile candidates (rows, columns of complex outputs), in its order
-SIMT_TILES = [(4, 4), (3, 4), (2, 4), (4, 3), (4, 2), (4, 7), (3, 7), (2, 7)]
+SIMT_TILES = [(4, 4), (3, 4), (2, 4), (4, 3), (4, 2), (4, 7), (3, 7), (2, 7), (2, 2), (1, 4), (1, 7), (1, 2)]
 
 
 def kernel_name(code, dtype):

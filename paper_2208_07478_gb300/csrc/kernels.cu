@@ -191,7 +191,10 @@ __global__ void zgemm_splitk_reduce(GemmDesc d, int ksplit, const typename cvec<
 struct TileShape {
     int tm, tn;
 };
-static const TileShape kShapes[] = {{4, 4}, {3, 4}, {2, 4}, {4, 3}, {4, 2}, {4, 7}, {3, 7}, {2, 7}};
+// (the last four serve contractions with few rows or columns: an o x o Fock block, a single
+// right-hand-side column block, ...)
+static const TileShape kShapes[] = {{4, 4}, {3, 4}, {2, 4}, {4, 3}, {4, 2}, {4, 7}, {3, 7}, {2, 7},
+                                    {2, 2}, {1, 4}, {1, 7}, {1, 2}};
 
 // Shape with the least padded work divided by the wave efficiency (whole waves of one CTA per
 // SM), with a slight preference for larger tiles (higher register reuse).
@@ -293,7 +296,11 @@ int launch_zgemm(const GemmDesc &d, const typename cvec<R>::T *A, const typename
     else if (s.tm == 4 && s.tn == 2) launch_shape<R, 4, 2>(d, A, B, C, st, ks, kchunk, work);
     else if (s.tm == 4 && s.tn == 7) launch_shape<R, 4, 7>(d, A, B, C, st, ks, kchunk, work);
     else if (s.tm == 3 && s.tn == 7) launch_shape<R, 3, 7>(d, A, B, C, st, ks, kchunk, work);
-    else launch_shape<R, 2, 7>(d, A, B, C, st, ks, kchunk, work);
+    else if (s.tm == 2 && s.tn == 7) launch_shape<R, 2, 7>(d, A, B, C, st, ks, kchunk, work);
+    else if (s.tm == 2 && s.tn == 2) launch_shape<R, 2, 2>(d, A, B, C, st, ks, kchunk, work);
+    else if (s.tm == 1 && s.tn == 4) launch_shape<R, 1, 4>(d, A, B, C, st, ks, kchunk, work);
+    else if (s.tm == 1 && s.tn == 7) launch_shape<R, 1, 7>(d, A, B, C, st, ks, kchunk, work);
+    else launch_shape<R, 1, 2>(d, A, B, C, st, ks, kchunk, work);
     if (ks > 1) {
         i64 n = (i64)d.M * d.N * d.batch;
         i64 g = ceil_div(n, 256);
