@@ -220,8 +220,10 @@ def gpu_arm(args):
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
+        torch.cuda.nvtx.range_push("timed")     # for profiler captures restricted to the timed region
         h = build()
         st = run_steps(h, prec, first + args.warmup, args.steps)
+        torch.cuda.nvtx.range_pop()
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier(pg, local)
