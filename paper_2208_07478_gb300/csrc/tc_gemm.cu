@@ -12,13 +12,16 @@
 // K-step issues three tcgen05.mma.kind::tf32 (hi*hi + hi*lo + lo*hi) accumulating in FP32, which
 // keeps the product near single-precision accuracy (the dropped lo*lo term is below 2^-22 relative).
 //
-// Shared memory holds each operand tile in the K-major, no-swizzle canonical layout of the MMA
-// descriptors: 8-row x 16-byte core matrices, 128 bytes apart along K (leading byte offset) and
-// 1024 bytes apart along M/N (stride byte offset). Two stages: the 256 threads stage tile s+1
-// (global loads, TF32 split, conflict-free 16-byte shared stores) while the MMAs of tile s run; one
-// thread issues the MMAs and commits them to the stage's mbarrier. Every wait is bounded: on timeout
-// the CTA records an error flag, stops issuing, waits (bounded) for its committed MMAs, frees its
-// TMEM and returns without writing C.
+// Three kernels share this arithmetic and differ in how operands reach shared memory:
+//  - tc_zgemm_kernel (register-fed, any A): 256 threads load both tiles, split them and store them
+//    in the K-major no-swizzle canonical layout (8-row x 16-byte core matrices, 128 B apart along K,
+//    1024 B apart along M/N), two stages; one thread issues the MMAs.
+//  - tc_zgemm_tma_kernel: A by TMA (128-byte swizzle) from TF32 hi / lo copies of the intermediate,
+//    B' staged by four producer warps, up to four stages.
+//  - tc_zgemm_bulk_kernel: A by TMA (64-byte swizzle) and B' by one cp.async.bulk per stage from an
+//    image expanded just before by bimage_kernel; no thread stages data, up to eight stages.
+// Every wait is bounded: on timeout the CTA records an error flag, stops issuing, waits (bounded)
+// for its issued copies and MMAs, frees its TMEM and returns without writing C.
 #include "ccgf_internal.h"
 #include <cuda.h>
 #include <algorithm>
