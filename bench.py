@@ -47,8 +47,10 @@ TF32_NOMINAL_RATIO = 1.1 / 2.25
 
 
 KERNEL_NAMES = {100: "tc_zgemm_tma_kernel", 101: "tc_zgemm_kernel", 102: "tc_zgemm_bulk_kernel"}
-# the SIMT launcher's per-thread tile candidates (rows, columns of complex outputs), in its order
-SIMT_TILES = [(4, 4), (3, 4), (2, 4), (4, 3), (4, 2), (4, 7), (3, 7), (2, 7), (2, 2), (1, 4), (1, 7), (1, 2)]
+# the SIMT launcher's tile candidates in its order: per-thread rows, columns of complex outputs,
+# thread rows of the CTA
+SIMT_TILES = [(4, 4, 16), (3, 4, 16), (2, 4, 16), (4, 3, 16), (4, 2, 16), (4, 7, 16), (3, 7, 16), (2, 7, 16),
+              (2, 2, 16), (1, 4, 16), (1, 7, 16), (1, 2, 16), (11, 2, 8), (3, 2, 8)]
 
 
 def kernel_name(code, dtype):
@@ -57,8 +59,8 @@ def kernel_name(code, dtype):
         return KERNEL_NAMES[code]
     if code <= 0:
         return f"zgemm_kernel<{dtype}>"
-    tm, tn = SIMT_TILES[code % 1000 - 1]
-    return f"zgemm_kernel<{dtype}, {tm}, {tn}>" + (f" split-K {code // 1000}" if code >= 1000 else "")
+    tm, tn, ty = SIMT_TILES[code % 1000 - 1]
+    return f"zgemm_kernel<{dtype}, {tm}, {tn}, {ty}>" + (f" split-K {code // 1000}" if code >= 1000 else "")
 
 
 def measured_peaks():

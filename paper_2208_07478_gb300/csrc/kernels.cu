@@ -54,21 +54,23 @@ template <typename T, typename S> __device__ __forceinline__ void cfma(T &acc, c
 }
 
 // ----------------------------------------------------------------------------- batched GEMM
-// (16 TM) x (16 TN) output tile per CTA, 256 threads, TM x TN complex outputs per thread (rows
-// ty + 16 i, columns tx + 16 j), K staged through shared memory 16 at a time. Loads pick the
-// coalesced mapping from whichever operand stride is 1. Out-of-range rows / columns of a tile
-// are zero-filled on load and masked on store. The launcher picks (TM, TN) per GEMM to keep
-// tile padding small (e.g. 88 rows -> 2 x 48 instead of 2 x 64).
-template <typename R, int TM, int TN>
+// (TY TM) x (TX TN) output tile per CTA, 256 threads as TY rows x TX = 256 / TY columns, TM x TN
+// complex outputs per thread (rows ty + TY i, columns tx + TX j), K staged through shared memory
+// 16 at a time. Loads pick the coalesced mapping from whichever operand stride is 1. Out-of-range
+// rows / columns of a tile are zero-filled on load and masked on store. The launcher picks
+// (TM, TN, TY) per GEMM to keep tile padding small (e.g. 88 rows -> 2 x 48 or 1 x 88).
+template <typename R, int TM, int TN, int TY = 16>
 __global__ void __launch_bounds__(256) zgemm_kernel(GemmDesc d, const typename cvec<R>::T *__restrict__ A,
                                                     const typename cvec<R>::T *__restrict__ B,
                                                     typename cvec<R>::T *__restrict__ C, int ksplit, int kchunk,
                                                     typename cvec<R>::T *__restrict__ work) {
     typedef typename cvec<R>::T T;
-    constexpr int BM = 16 * TM, BN = 16 * TN, BK = 16;
+    constexpr int TX = 256 / TY;
+    constexpr int BM = TY * TM, BN = TX * TN, BK = 16;
+    constexpr int NLA = (BM * BK + 255) / 256, NLB = (BN * BK + 255) / 256;   // tile loads per thread
     __shared__ T As[BK][BM];
     __shared__ T Bs[BK][BN];
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const T alpha = {(R)d.alpha.x, (R)d.alpha.y};
     const T beta = {(R)d.beta.x, (R)d.beta.y};
@@ -90,15 +92,17 @@ __global__ void __launch_bounds__(256) zgemm_kernel(GemmDesc d, const typename c
             const T *Bb = B + d.offB[(i64)b * d.nred + r];
             for (int k0 = kbeg; k0 < kend; k0 += BK) {
 #pragma unroll
-                for (int s = 0; s < TM; ++s) {
+                for (int s = 0; s < NLA; ++s) {
                     int l = tid + 256 * s, i, kk;
+                    if (BM * BK % 256 != 0 && l >= BM * BK) break;
                     if (d.csA == 1) { kk = l & 15; i = l >> 4; } else { i = l % BM; kk = l / BM; }
                     int m = m0 + i, k = k0 + kk;
                     As[kk][i] = (m < d.M && k < kend) ? Ab[(i64)m * d.rsA + (i64)k * d.csA] : cz<T>();
                 }
 #pragma unroll
-                for (int s = 0; s < TN; ++s) {
+                for (int s = 0; s < NLB; ++s) {
                     int l = tid + 256 * s, nn, kk;
+                    if (BN * BK % 256 != 0 && l >= BN * BK) break;
                     if (d.csB == 1) { nn = l % BN; kk = l / BN; } else { kk = l & 15; nn = l >> 4; }
                     int n = n0 + nn, k = k0 + kk;
                     Bs[kk][nn] = (n < d.N && k < kend) ? Bb[(i64)k * d.rsB + (i64)n * d.csB] : cz<T>();
@@ -108,9 +112,9 @@ __global__ void __launch_bounds__(256) zgemm_kernel(GemmDesc d, const typename c
                 for (int kk = 0; kk < BK; ++kk) {
                     T a[TM], bb[TN];
 #pragma unroll
-                    for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + 16 * i];
+                    for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + TY * i];
 #pragma unroll
-                    for (int j = 0; j < TN; ++j) bb[j] = Bs[kk][tx + 16 * j];
+                    for (int j = 0; j < TN; ++j) bb[j] = Bs[kk][tx + TX * j];
 #pragma unroll
                     for (int i = 0; i < TM; ++i)
 #pragma unroll
@@ -124,11 +128,11 @@ __global__ void __launch_bounds__(256) zgemm_kernel(GemmDesc d, const typename c
             T *Wb = work + ((i64)b * ksplit + ks) * (i64)d.M * d.N;
 #pragma unroll
             for (int i = 0; i < TM; ++i) {
-                int m = m0 + ty + 16 * i;
+                int m = m0 + ty + TY * i;
                 if (m >= d.M) continue;
 #pragma unroll
                 for (int j = 0; j < TN; ++j) {
-                    int n = n0 + tx + 16 * j;
+                    int n = n0 + tx + TX * j;
                     if (n < d.N) Wb[(i64)m * d.N + n] = acc[i][j];
                 }
             }
@@ -137,11 +141,11 @@ __global__ void __launch_bounds__(256) zgemm_kernel(GemmDesc d, const typename c
         T *Cb = C + d.offC[b];
 #pragma unroll
         for (int i = 0; i < TM; ++i) {
-            int m = m0 + ty + 16 * i;
+            int m = m0 + ty + TY * i;
             if (m >= d.M) continue;
 #pragma unroll
             for (int j = 0; j < TN; ++j) {
-                int n = n0 + tx + 16 * j;
+                int n = n0 + tx + TX * j;
                 if (n >= d.N) continue;
                 T *c = Cb + (i64)m * d.rsC + (i64)n * d.csC;
                 T v;
@@ -189,12 +193,14 @@ __global__ void zgemm_splitk_reduce(GemmDesc d, int ksplit, const typename cvec<
 
 // Per-thread tile shapes available to the launcher (rows x columns of complex outputs).
 struct TileShape {
-    int tm, tn;
+    int tm, tn, ty;   // per-thread rows, columns; thread rows of the CTA (16 or 8)
+    i64 bm() const { return (i64)ty * tm; }
+    i64 bn() const { return (i64)(256 / ty) * tn; }
 };
-// (the last four serve contractions with few rows or columns: an o x o Fock block, a single
-// right-hand-side column block, ...)
-static const TileShape kShapes[] = {{4, 4}, {3, 4}, {2, 4}, {4, 3}, {4, 2}, {4, 7}, {3, 7}, {2, 7},
-                                    {2, 2}, {1, 4}, {1, 7}, {1, 2}};
+// (the 9th-12th serve contractions with few rows or columns: an o x o Fock block, a single
+// right-hand-side column block, ...; the last two have 8-row granularity: 88 or 24 rows exactly)
+static const TileShape kShapes[] = {{4, 4, 16}, {3, 4, 16}, {2, 4, 16}, {4, 3, 16}, {4, 2, 16}, {4, 7, 16}, {3, 7, 16},
+                                    {2, 7, 16}, {2, 2, 16}, {1, 4, 16}, {1, 7, 16}, {1, 2, 16}, {11, 2, 8}, {3, 2, 8}};
 
 // Shape with the least padded work divided by the wave efficiency (whole waves of one CTA per
 // SM), with a slight preference for larger tiles (higher register reuse).
@@ -205,12 +211,12 @@ static TileShape pick_shape(const GemmDesc &d) {
     TileShape best = kShapes[0];
     double best_cost = 1e300;
     for (const TileShape &s : kShapes) {
-        const i64 bm = 16 * s.tm, bn = 16 * s.tn;
+        const i64 bm = s.bm(), bn = s.bn();
         const double padded = (double)ceil_div(d.M, bm) * bm * (double)ceil_div(d.N, bn) * bn;
         const double ctas = (double)ceil_div(d.M, bm) * ceil_div(d.N, bn) * d.batch;
         const double waves = ctas / 152.0;
         const double wave_eff = waves >= 1.0 ? waves / std::ceil(waves) : waves;
-        const double cost = padded / wave_eff * (1.0 + 0.02 * (16.0 / (s.tm * s.tn)));
+        const double cost = padded / wave_eff * (1.0 + 0.02 * (16.0 / (s.tm * s.tn * (16.0 / s.ty))));
         if (cost < best_cost) {
             best_cost = cost;
             best = s;
@@ -232,7 +238,7 @@ int zgemm_ksplit(const GemmDesc &d) {
     }
     // Enough CTAs to cover the SMs twice; every split keeps at least 8 k-tiles of work.
     const TileShape s = pick_shape(d);
-    const i64 tiles = ceil_div(d.M, 16 * s.tm) * ceil_div(d.N, 16 * s.tn) * (i64)d.batch;
+    const i64 tiles = ceil_div(d.M, s.bm()) * ceil_div(d.N, s.bn()) * (i64)d.batch;
     if (tiles >= 304 || d.nred != 1) return 1;
     i64 k = ceil_div(304, tiles);
     i64 kmax = d.K / 128;
@@ -246,7 +252,7 @@ int zgemm_wave_split(const GemmDesc &d, int tile) {
     GemmDesc e = d;
     e.tile = tile;
     const TileShape s = pick_shape(e);
-    const double ctas = (double)ceil_div(d.M, 16 * s.tm) * ceil_div(d.N, 16 * s.tn) * d.batch;
+    const double ctas = (double)ceil_div(d.M, s.bm()) * ceil_div(d.N, s.bn()) * d.batch;
     auto eff = [&](int k) {
         const double w = ctas * k / 152.0;
         return w / std::ceil(w);
@@ -269,12 +275,12 @@ i64 zgemm_workspace_elems(const GemmDesc &d) {
     return s > 1 ? (i64)s * d.M * d.N * d.batch : 0;
 }
 
-template <typename R, int TM, int TN>
+template <typename R, int TM, int TN, int TY = 16>
 static void launch_shape(const GemmDesc &d, const typename cvec<R>::T *A, const typename cvec<R>::T *B, typename cvec<R>::T *C,
                          cudaStream_t st, int ks, int kchunk, typename cvec<R>::T *work) {
     i64 z = (i64)d.batch * ks;
-    dim3 grid((unsigned)ceil_div(d.N, 16 * TN), (unsigned)ceil_div(d.M, 16 * TM), (unsigned)(z < 65535 ? z : 65535));
-    zgemm_kernel<R, TM, TN><<<grid, 256, 0, st>>>(d, A, B, C, ks, kchunk, work);
+    dim3 grid((unsigned)ceil_div(d.N, (256 / TY) * TN), (unsigned)ceil_div(d.M, TY * TM), (unsigned)(z < 65535 ? z : 65535));
+    zgemm_kernel<R, TM, TN, TY><<<grid, 256, 0, st>>>(d, A, B, C, ks, kchunk, work);
 }
 
 template <typename R>
@@ -300,6 +306,8 @@ int launch_zgemm(const GemmDesc &d, const typename cvec<R>::T *A, const typename
     else if (s.tm == 2 && s.tn == 2) launch_shape<R, 2, 2>(d, A, B, C, st, ks, kchunk, work);
     else if (s.tm == 1 && s.tn == 4) launch_shape<R, 1, 4>(d, A, B, C, st, ks, kchunk, work);
     else if (s.tm == 1 && s.tn == 7) launch_shape<R, 1, 7>(d, A, B, C, st, ks, kchunk, work);
+    else if (s.tm == 11 && s.tn == 2 && s.ty == 8) launch_shape<R, 11, 2, 8>(d, A, B, C, st, ks, kchunk, work);
+    else if (s.tm == 3 && s.tn == 2 && s.ty == 8) launch_shape<R, 3, 2, 8>(d, A, B, C, st, ks, kchunk, work);
     else launch_shape<R, 1, 2>(d, A, B, C, st, ks, kchunk, work);
     if (ks > 1) {
         i64 n = (i64)d.M * d.N * d.batch;
