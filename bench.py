@@ -46,7 +46,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 TF32_NOMINAL_RATIO = 1.1 / 2.25
 
 
-KERNEL_NAMES = {100: "tc_zgemm_tma_kernel", 101: "tc_zgemm_kernel", 102: "tc_zgemm_bulk_kernel"}
+KERNEL_NAMES = {100: "tc_zgemm_tma_kernel", 101: "tc_zgemm_kernel", 102: "tc_zgemm_bulk_kernel", 200: "zgemm_smallm_kernel"}
 # the SIMT launcher's tile candidates in its order: per-thread rows, columns of complex outputs,
 # thread rows of the CTA
 SIMT_TILES = [(4, 4, 16), (3, 4, 16), (2, 4, 16), (4, 3, 16), (4, 2, 16), (4, 7, 16), (3, 7, 16), (2, 7, 16),
@@ -61,6 +61,16 @@ def kernel_name(code, dtype):
         return f"zgemm_kernel<{dtype}>"
     tm, tn, ty = SIMT_TILES[code % 1000 - 1]
     return f"zgemm_kernel<{dtype}, {tm}, {tn}, {ty}>" + (f" split-K {code // 1000}" if code >= 1000 else "")
+
+
+def gemm_kernel_sha():
+    """sha256 of the SIMT GEMM kernel's source (the template definition in kernels.cu): a stored
+    DRAM-traffic figure is used only while the kernel it was measured on is unchanged."""
+    import hashlib
+    src = open(os.path.join(ROOT, "paper_2208_07478_gb300", "csrc", "kernels.cu")).read()
+    start = src.index("template <typename R, int TM, int TN, int TY = 16>\n__global__")
+    end = src.index("\n}\n", start) + 3
+    return hashlib.sha256(src[start:end].encode()).hexdigest()
 
 
 def measured_peaks():
@@ -261,10 +271,9 @@ def gpu_arm(args):
     if os.path.exists(tfile):
         try:
             tinfo = json.load(open(tfile))
-            import hashlib
-            src = open(os.path.join(ROOT, "paper_2208_07478_gb300", "csrc", "kernels.cu"), "rb").read()
-            same_kernel = tinfo.get("kernels_cu_sha256") == hashlib.sha256(src).hexdigest()
-            if same_kernel and tinfo.get("kernel_step") == top[0] and tinfo.get("precision") == "fp64":
+            same = (tinfo.get("kernel_source_sha256") == gemm_kernel_sha() and tinfo.get("kernel") == kernel_name(top[3], "double")
+                    and tinfo.get("kernel_step") == top[0] and tinfo.get("precision") == "fp64")
+            if same:
                 roof["traffic"] = tinfo.get("dram_bytes_per_launch")
                 roof["traffic_source"] = tinfo.get("source")
         except (OSError, ValueError):

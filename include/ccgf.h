@@ -208,7 +208,7 @@ ccgf_status ccgf_sigma_ip_noalloc(ccgf_handle *h, int kshift, long long nvec, co
 /* GEMM kernel selection (no counterpart in the paper). With autotuning on (the default; the
  * environment variable CCGF_AUTOTUNE=0 starts it off), the first run of a sigma plan times every
  * candidate kernel of each contraction (the SIMT tile shapes, each also with the K split that best
- * fills whole waves of the GPU, and, for CCGF_TF32X3, the three
+ * fills whole waves of the GPU, the few-row kernel where it applies, and, for CCGF_TF32X3, the three
  * tensor-core kernels) on the real operands and keeps the fastest; the choice is cached for the
  * process by shape, so it is measured once. Off: the launcher's model picks the SIMT tile and
  * CCGF_TF32X3 uses the tensor cores wherever the shape allows. Process-wide; affects plans built
@@ -217,7 +217,8 @@ void ccgf_set_autotune(int enable);
 /* Kernel chosen for plan step `step` of the (sector, kshift) plan at precision prec:
  * -1 not a contraction (or no such step / plan), 0 not tuned (defaults apply), 1..99 the SIMT
  * kernel with the launcher's k-th tile shape, k + 1000 s the same kernel with K split over s
- * thread blocks (partial sums reduced by a second kernel), 100 the tensor-core kernel with A by TMA and B
+ * thread blocks (partial sums reduced by a second kernel), 200 the few-row kernel (one thread
+ * per output column, for at most 8 rows and a short reduction), 100 the tensor-core kernel with A by TMA and B
  * staged by producer warps, 101 the register-fed tensor-core kernel, 102 the tensor-core kernel
  * with both operands by asynchronous copies (B from a pre-expanded image). */
 int ccgf_sigma_step_kernel(const ccgf_handle *h, int sector, int kshift, int step, ccgf_precision prec);

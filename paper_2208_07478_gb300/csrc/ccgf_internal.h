@@ -64,6 +64,11 @@ int zgemm_ksplit(const GemmDesc &d);
 int zgemm_wave_split(const GemmDesc &d, int tile);
 i64 zgemm_workspace_elems(const GemmDesc &d);   // split-K partials needed (0 without a split)
 // returns the number of kernels launched
+// few-row kernel (M <= 8, K nred <= 256): one thread per output column; returns 0 if not applicable
+bool zgemm_smallm_supported(const GemmDesc &d);
+template <typename R>
+int launch_zgemm_smallm(const GemmDesc &d, const typename cvec<R>::T *A, const typename cvec<R>::T *B,
+                        typename cvec<R>::T *C, cudaStream_t st);
 template <typename R>
 int launch_zgemm(const GemmDesc &d, const typename cvec<R>::T *A, const typename cvec<R>::T *B,
                  typename cvec<R>::T *C, cudaStream_t st, typename cvec<R>::T *work = nullptr, i64 work_elems = 0);

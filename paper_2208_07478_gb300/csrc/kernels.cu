@@ -317,6 +317,66 @@ int launch_zgemm(const GemmDesc &d, const typename cvec<R>::T *A, const typename
     }
     return 1;
 }
+
+// Contractions with at most 8 rows and a short reduction (an o x o Fock block applied to every
+// column, for instance) are bound by streaming B and C: one thread per output column keeps the
+// M partial sums in registers and reads each B element once; A (at most 8 x K) is re-read from
+// cache. Coalesced when B and C have unit column stride.
+template <typename R>
+__global__ void __launch_bounds__(256) zgemm_smallm_kernel(GemmDesc d, const typename cvec<R>::T *__restrict__ A,
+                                                           const typename cvec<R>::T *__restrict__ B,
+                                                           typename cvec<R>::T *__restrict__ C) {
+    typedef typename cvec<R>::T T;
+    constexpr int MM = 8;
+    const i64 total = (i64)d.batch * d.N;
+    const bool use_beta = (d.beta.x != 0.0 || d.beta.y != 0.0);
+    for (i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (i64)gridDim.x * blockDim.x) {
+        const int b = (int)(t / d.N), n = (int)(t - (i64)b * d.N);
+        T acc[MM];
+#pragma unroll
+        for (int m = 0; m < MM; ++m) acc[m] = cz<T>();
+        for (int r = 0; r < d.nred; ++r) {
+            const T *Ab = A + d.offA[(i64)b * d.nred + r];
+            const T *Bb = B + d.offB[(i64)b * d.nred + r] + (i64)n * d.csB;
+            for (int k = 0; k < d.K; ++k) {
+                const T bv = Bb[(i64)k * d.rsB];
+#pragma unroll
+                for (int m = 0; m < MM; ++m)
+                    if (m < d.M) cfma<T, R>(acc[m], Ab[(i64)m * d.rsA + (i64)k * d.csA], bv);
+            }
+        }
+        T *Cb = C + d.offC[b] + (i64)n * d.csC;
+#pragma unroll
+        for (int m = 0; m < MM; ++m) {
+            if (m >= d.M) break;
+            T *c = Cb + (i64)m * d.rsC;
+            T v;
+            v.x = (R)d.alpha.x * acc[m].x - (R)d.alpha.y * acc[m].y;
+            v.y = (R)d.alpha.x * acc[m].y + (R)d.alpha.y * acc[m].x;
+            if (use_beta) {
+                const T o = *c;
+                v.x += (R)d.beta.x * o.x - (R)d.beta.y * o.y;
+                v.y += (R)d.beta.x * o.y + (R)d.beta.y * o.x;
+            }
+            *c = v;
+        }
+    }
+}
+
+bool zgemm_smallm_supported(const GemmDesc &d) {
+    return d.M >= 1 && d.M <= 8 && d.N >= 1 && d.batch >= 1 && (i64)d.K * d.nred <= 256;
+}
+
+template <typename R>
+int launch_zgemm_smallm(const GemmDesc &d, const typename cvec<R>::T *A, const typename cvec<R>::T *B,
+                        typename cvec<R>::T *C, cudaStream_t st) {
+    if (!zgemm_smallm_supported(d)) return 0;
+    const i64 g = ceil_div((i64)d.batch * d.N, 256);
+    zgemm_smallm_kernel<R><<<(unsigned)(g > 152 * 16 ? 152 * 16 : g), 256, 0, st>>>(d, A, B, C);
+    return 1;
+}
+template int launch_zgemm_smallm<double>(const GemmDesc &, const double2 *, const double2 *, double2 *, cudaStream_t);
+template int launch_zgemm_smallm<float>(const GemmDesc &, const float2 *, const float2 *, float2 *, cudaStream_t);
 template int launch_zgemm<double>(const GemmDesc &, const double2 *, const double2 *, double2 *, cudaStream_t, double2 *, i64);
 template int launch_zgemm<float>(const GemmDesc &, const float2 *, const float2 *, float2 *, cudaStream_t, float2 *, i64);
 

@@ -625,8 +625,9 @@ inline unsigned gsz(i64 n) {
 // GEMM kernel choices of a plan step: 0 = default (the bulk-fed tensor-core kernel when the A
 // operand is TMA-addressable, else the register-fed one; SIMT tile by the launcher's model),
 // k in 1..zgemm_tile_count() = SIMT kernel with the launcher's k-th tile, k + 1000 s = the same
-// with K split over s CTAs (s >= 2, partial sums reduced by a second kernel), or one of these three
-enum { CHOICE_TC_TMA = 100, CHOICE_TC_REG = 101, CHOICE_TC_BULK = 102, CHOICE_SPLIT = 1000 };
+// with K split over s CTAs (s >= 2, partial sums reduced by a second kernel), the few-row kernel
+// (200), or one of the three tensor-core kernels (100-102)
+enum { CHOICE_TC_TMA = 100, CHOICE_TC_REG = 101, CHOICE_TC_BULK = 102, CHOICE_SMALLM = 200, CHOICE_SPLIT = 1000 };
 
 // one GEMM step with the given choice; returns the number of launches (0: choice not applicable)
 template <typename R>
@@ -641,8 +642,9 @@ int run_gemm_step(ccgf_handle *h, const SigmaPlan *P, const SigmaStep &s, int ch
     d.offB = offs + s.offB_pos;
     d.offC = offs + s.offC_pos;
     const T *A = f64 ? (const T *)h->W[s.a_buf].p : (const T *)h->Wf[s.a_buf].p;
+    if (choice == CHOICE_SMALLM) return launch_zgemm_smallm<R>(d, A, scr, C, st);
     if constexpr (sizeof(R) == 4) {
-        if (tensor_cores && tc_zgemm_supported(d) && (choice == 0 || choice >= CHOICE_TC_TMA)) {
+        if (tensor_cores && tc_zgemm_supported(d) && (choice == 0 || (choice >= CHOICE_TC_TMA && choice < CHOICE_SMALLM))) {
             int n = 0;
             if ((choice == 0 || choice == CHOICE_TC_BULK) && s.rowA_pos >= 0)
                 n = launch_tc_zgemm_bulk(h, s.a_buf, d, offs + s.rowA_pos, offs + s.bslot_pos, offs + s.bsrc_pos, s.nslots, scr, C,
@@ -665,7 +667,8 @@ int run_gemm_step(ccgf_handle *h, const SigmaPlan *P, const SigmaStep &s, int ch
     return launch_zgemm<R>(d, A, scr, C, st, scr + P->seg[SEG_SPLITK], P->seg[SEG_END] - P->seg[SEG_SPLITK]);
 }
 
-// Measured kernel choice per GEMM step (an autotuner): every candidate (the SIMT tiles and, for
+// Measured kernel choice per GEMM step (an autotuner): every candidate (the SIMT tiles, the few-row
+// kernel where it applies and, for
 // CCGF_TF32X3, the two tensor-core kernels) runs once to warm up and twice timed with CUDA
 // events on the real operands; the fastest is kept in the step and in a process-wide table keyed
 // by the GEMM's shape, strides and precision, so later plans and handles reuse it without timing.
@@ -747,6 +750,7 @@ ccgf_status autotune_plan(ccgf_handle *h, SigmaPlan *P, int pi, bool tensor_core
             const int ks = zgemm_wave_split(g, t);
             if (ks > 1) cand.push_back(t + CHOICE_SPLIT * ks);
         }
+        if (zgemm_smallm_supported(g)) cand.push_back(CHOICE_SMALLM);
         if (sizeof(R) == 4 && tensor_cores && tc_zgemm_supported(g)) {
             cand.push_back(CHOICE_TC_REG);
             if (s.rowA_pos >= 0) {
