@@ -23,8 +23,13 @@
  *       EA: r1[a] (nvir), then r2[kj][ka][j][a][b] with k_b = K + kj - ka.
  *     dim_ip = nocc + nk^2 nocc^2 nvir, dim_ea = nvir + nk^2 nocc nvir^2.
  *   - Every call is stream-ordered on the caller's CUDA stream (cudaStream_t
- *     passed as void*; NULL = the legacy default stream). Only ccgf_solve_gf
- *     synchronises (once per GMRES cycle, to read convergence flags).
+ *     passed as void*; NULL = the legacy default stream). A call synchronises
+ *     the stream only where stated: ccgf_solve_gf reads the convergence flags
+ *     once per Arnoldi step; a sigma call synchronises only when it first meets
+ *     a new vector count or momentum (plan and workspace set-up, which may
+ *     allocate) and, with CCGF_TF32X3, once at its end to read the tensor-core
+ *     error flag. Repeated FP64 / FP32 sigma calls of one shape allocate
+ *     nothing and do not synchronise.
  *   - Errors are returned as status codes; nothing aborts, throws or traps.
  *     ccgf_last_error() gives a message for the last failing call on this
  *     thread. One handle per host thread.
@@ -52,8 +57,9 @@ typedef enum {
     CCGF_TF32X3 = 2      /* sigma contractions on the tensor cores (tcgen05): each FP32 operand split
                             into two TF32 parts, three products (hi*hi + hi*lo + lo*hi) accumulated
                             in FP32, inside FP64 refinement; contractions too small for a 128-row
-                            tile run as in CCGF_FP32. A tensor-core wait that runs past its 2 s
-                            limit makes the call return CCGF_ERR_TIMEOUT. */
+                            tile run as in CCGF_FP32. A tensor-core wait that runs past its limit
+                            (ccgf_options::device_wait_timeout_ms) makes the call return
+                            CCGF_ERR_TIMEOUT. */
 } ccgf_precision;
 
 typedef enum { CCGF_SECTOR_IP = 1, CCGF_SECTOR_EA = 2, CCGF_SECTOR_BOTH = 3 } ccgf_sector;
@@ -82,7 +88,10 @@ typedef struct {
     int max_iter;             /* cap on inner iterations per right-hand side              */
     int max_refine;           /* cap on FP64 true-residual checks (refinement cycles)      */
     int omega_chunk;          /* frequencies solved together per (sector, K) batch         */
-    double device_wait_timeout_ms; /* reserved for bounded device waits                   */
+    double device_wait_timeout_ms; /* bound of every tensor-core device wait, (0, 60000] ms;
+                                      a wait that runs out makes the call return
+                                      CCGF_ERR_TIMEOUT. Build: the handle's bound for sigma
+                                      calls; solve: the bound during that solve.           */
     int warm_start;           /* 1: initial vectors from the trained warm-start network
                                  (ccgf_train_warmstart), kept per column only when their true
                                  residual is below the cold start's |b|                    */
@@ -109,7 +118,7 @@ typedef struct {
 typedef struct ccgf_handle ccgf_handle;
 
 /* Default options: FP64, tol 1e-10, restart 30, max_iter 2000, max_refine 20, omega_chunk 1,
- * no warm start. */
+ * device waits bounded at 1000 ms, no warm start. */
 void ccgf_default_options(ccgf_options *opt);
 
 /* Build the similarity-transformed Hamiltonian blocks (Eq. 5) for the EOM-CCSD
@@ -125,8 +134,12 @@ ccgf_status ccgf_dims(const ccgf_handle *h, int *nk, int *nocc, int *nvir,
 
 /* y = A_IP x (Eq. 8, removal part): the connected EOM-IP-CCSD operator H_bar - E
  * on nvec vectors at total momentum kshift. x, y: device complex [nvec][dim_ip],
- * caller-owned, must not alias. prec selects FP64 or FP32 arithmetic (inputs and
- * outputs stay FP64). Errors: INVALID_ARG (kshift, nvec, NULL), OOM (workspace), CUDA. */
+ * caller-owned, must not alias. prec selects the arithmetic of the contractions
+ * (inputs and outputs stay FP64). The handle keeps its transpose buffers, plans and
+ * scratch between calls: the first call with a new nvec (or kshift) allocates and
+ * synchronises, later calls of that shape only enqueue kernels (CCGF_TF32X3 then
+ * synchronises once to read the tensor-core error flag). Errors: INVALID_ARG
+ * (kshift, nvec, NULL), OOM (workspace), CUDA, TIMEOUT (CCGF_TF32X3 wait bound). */
 ccgf_status ccgf_sigma_ip(ccgf_handle *h, int kshift, long long nvec, const double *x,
                           double *y, ccgf_precision prec, void *stream);
 
@@ -229,6 +242,11 @@ int ccgf_sigma_step_kernel(const ccgf_handle *h, int sector, int kshift, int ste
  * wait gave up as designed (the CUDA context stays usable), CCGF_OK if it did not. Synchronises
  * the stream. */
 ccgf_status ccgf_tensor_wait_selftest(double limit_ms, void *stream);
+
+/* Failure injection for error-path tests (no counterpart in the paper): after `after` more
+ * successful device allocations, every allocation of the library fails with CCGF_ERR_OOM
+ * (without calling cudaMalloc) until the hook is reset with after = -1. Process-wide. */
+void ccgf_inject_alloc_failure(long long after);
 
 /* Number of kernels this handle has launched since it was built (build included). */
 long long ccgf_launch_count(const ccgf_handle *h);

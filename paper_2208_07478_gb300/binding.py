@@ -48,7 +48,7 @@ class Stats(C.Structure):
 
 EXPORTS = ["ccgf_default_options", "ccgf_build_intermediates", "ccgf_dims", "ccgf_sigma_ip", "ccgf_sigma_ea",
            "ccgf_rhs", "ccgf_left", "ccgf_solve_gf", "ccgf_sigma_profile", "ccgf_sigma_step_name", "ccgf_sigma_ip_noalloc", "ccgf_launch_count",
-           "ccgf_set_autotune", "ccgf_sigma_step_kernel", "ccgf_tensor_wait_selftest",
+           "ccgf_set_autotune", "ccgf_sigma_step_kernel", "ccgf_tensor_wait_selftest", "ccgf_inject_alloc_failure",
            "ccgf_train_warmstart", "ccgf_mlp_param_count", "ccgf_mlp_forward", "ccgf_mlp_loss_grad", "ccgf_destroy",
            "ccgf_status_string", "ccgf_last_error"]
 
@@ -98,6 +98,8 @@ def load(path: str | None = None):
     lib.ccgf_launch_count.restype = ll
     lib.ccgf_tensor_wait_selftest.argtypes = [C.c_double, vp]
     lib.ccgf_tensor_wait_selftest.restype = C.c_int
+    lib.ccgf_inject_alloc_failure.argtypes = [C.c_longlong]
+    lib.ccgf_inject_alloc_failure.restype = None
     lib.ccgf_set_autotune.argtypes = [C.c_int]
     lib.ccgf_set_autotune.restype = None
     lib.ccgf_sigma_step_kernel.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int]
@@ -225,6 +227,11 @@ KERNEL_TC_TMA, KERNEL_TC_REG, KERNEL_TC_BULK = 100, 101, 102
 def tensor_wait_selftest(limit_ms=50.0, stream=None):
     """Status of ccgf_tensor_wait_selftest (CCGF_ERR_TIMEOUT when the bounded wait gave up as designed)."""
     return int(load().ccgf_tensor_wait_selftest(float(limit_ms), _stream_ptr(stream)))
+
+
+def inject_alloc_failure(after):
+    """ccgf_inject_alloc_failure: make the library's allocations fail after `after` more (-1 resets)."""
+    load().ccgf_inject_alloc_failure(int(after))
 
 
 def sigma_ip_noalloc(h: Handle, kshift, x, y, stream=None):

@@ -16,6 +16,9 @@ __global__ void conj_kernel(const double2 *a, double2 *b, i64 n) {
     for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) b[i] = make_double2(a[i].x, -a[i].y);
 }
 
+bool valid_wait(double ms) { return ms > 0.0 && ms <= 60000.0; }
+unsigned long long wait_ns_of(double ms) { return (unsigned long long)(ms * 1e6); }
+
 void destroy(ccgf_handle *h) {
     if (!h) return;
     warmstart_free(h);
@@ -41,6 +44,9 @@ void destroy(ccgf_handle *h) {
     dfree(h->tc_err);
     dfree(h->splitw64);
     dfree(h->splitw32);
+    dfree(h->zero_tab);
+    dfree(h->abi_x);
+    dfree(h->abi_y);
     tc_free(h);
     delete h;
 }
@@ -75,8 +81,11 @@ const char *ccgf_status_string(ccgf_status s) {
 }
 
 ccgf_status ccgf_build_intermediates(const ccgf_system *sys, const ccgf_options *opt, void *stream, ccgf_handle **out) {
-    (void)opt;
     if (!sys || !out) { set_last_error("NULL system or output pointer"); return CCGF_ERR_INVALID_ARG; }
+    if (opt && !valid_wait(opt->device_wait_timeout_ms)) {
+        set_last_error("device_wait_timeout_ms must be in (0, 60000]");
+        return CCGF_ERR_INVALID_ARG;
+    }
     *out = nullptr;
     if (sys->kmesh[0] < 1 || sys->kmesh[1] < 1 || sys->kmesh[2] < 1 || sys->nocc < 1 || sys->nvir < 1 || sys->naux < 1) {
         set_last_error("kmesh, nocc, nvir and naux must be >= 1");
@@ -87,6 +96,7 @@ ccgf_status ccgf_build_intermediates(const ccgf_system *sys, const ccgf_options 
     if (!h) { set_last_error("host allocation failed"); return CCGF_ERR_OOM; }
     cudaStream_t st = (cudaStream_t)stream;
     cudaGetDevice(&h->device);
+    if (opt) h->wait_ns = wait_ns_of(opt->device_wait_timeout_ms);
     h->km.init(sys->kmesh);
     h->nk = h->km.nk;
     h->o = sys->nocc;
@@ -145,18 +155,16 @@ static ccgf_status sigma_abi(ccgf_handle *h, int sector, int kshift, long long n
     cudaStream_t st = (cudaStream_t)stream;
     const i64 D = sector == CCGF_SECTOR_IP ? h->dim_ip : h->dim_ea;
     const int nv = (int)nvec;
-    DBuf<double2> xt, yt;
-    CCGF_TRY(dalloc(xt, D * nv));
-    ccgf_status s = dalloc(yt, D * nv);
-    if (s != CCGF_OK) { dfree(xt); return s; }
-    launch_transpose_in((const double2 *)x, xt.p, D, nv, nv, st);
-    s = sigma_apply(h, sector, kshift, nv, xt.p, yt.p, prec, st);
-    if (s == CCGF_OK) launch_transpose_out(yt.p, (double2 *)y, D, nv, nv, st);
-    cudaError_t e = cudaStreamSynchronize(st);
-    dfree(xt);
-    dfree(yt);
-    if (s != CCGF_OK) return s;
-    if (e != cudaSuccess) { set_last_error(cudaGetErrorString(e)); return CCGF_ERR_CUDA; }
+    if (h->abi_x.n < D * nv) {
+        // grow the handle's transpose buffers (cudaFree waits for work that may still read them)
+        CCGF_TRY(dalloc(h->abi_x, D * nv));
+        CCGF_TRY(dalloc(h->abi_y, D * nv));
+    }
+    launch_transpose_in((const double2 *)x, h->abi_x.p, D, nv, nv, st);
+    CCGF_TRY(sigma_apply(h, sector, kshift, nv, h->abi_x.p, h->abi_y.p, prec, st));
+    launch_transpose_out(h->abi_y.p, (double2 *)y, D, nv, nv, st);
+    h->launches += 2;
+    CCGF_CUDA_TRY(cudaGetLastError());
     if (prec == CCGF_TF32X3) return tc_error_check(h, st);
     return CCGF_OK;
 }
@@ -196,6 +204,14 @@ ccgf_status ccgf_solve_gf(ccgf_handle *h, int sectors, int nomega, const double 
         return CCGF_ERR_INVALID_ARG;
     }
     if (o.prec != CCGF_FP64 && o.prec != CCGF_FP32 && o.prec != CCGF_TF32X3) { set_last_error("unknown precision"); return CCGF_ERR_INVALID_ARG; }
+    if (!valid_wait(o.device_wait_timeout_ms)) { set_last_error("device_wait_timeout_ms must be in (0, 60000]"); return CCGF_ERR_INVALID_ARG; }
+    // the solve's own wait bound for its duration; the handle's build-time bound afterwards
+    struct WaitScope {
+        ccgf_handle *h;
+        unsigned long long saved;
+        ~WaitScope() { h->wait_ns = saved; }
+    } scope{h, h->wait_ns};
+    h->wait_ns = wait_ns_of(o.device_wait_timeout_ms);
     return solve_gf(h, sectors, nomega, omega, eta, &o, G_out, G_on_device, stats, (cudaStream_t)stream);
 }
 
@@ -204,12 +220,21 @@ ccgf_status ccgf_sigma_profile(ccgf_handle *h, int sector, int kshift, long long
                                int *nsteps) {
     if (!h || !step_ms || !step_flops || !nsteps || max_steps < 1) { set_last_error("NULL output or max_steps < 1"); return CCGF_ERR_INVALID_ARG; }
     if (sector != CCGF_SECTOR_IP && sector != CCGF_SECTOR_EA) { set_last_error("sector must be IP or EA"); return CCGF_ERR_INVALID_ARG; }
-    std::vector<cudaEvent_t> ev(max_steps + 1);
+    std::vector<cudaEvent_t> ev(max_steps + 1, nullptr);
+    auto cleanup = on_scope_exit([&] {
+        h->prof_events = nullptr;
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+    });
     for (auto &e : ev) CCGF_CUDA_TRY(cudaEventCreate(&e));
     h->prof_events = ev.data();
     h->prof_max = max_steps + 1;
     h->prof_count = 0;
     ccgf_status s = sigma_abi(h, sector, kshift, nvec, x, y, prec, stream);
+    if (s == CCGF_OK && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
+        set_last_error("stream synchronisation after the profiled sigma failed");
+        s = CCGF_ERR_CUDA;
+    }
     h->prof_events = nullptr;
     int n = plan_step_count(h, sector, kshift);
     *nsteps = n;
@@ -221,7 +246,6 @@ ccgf_status ccgf_sigma_profile(ccgf_handle *h, int sector, int kshift, long long
             step_flops[i] = plan_step_flops(h, sector, kshift, i);
         }
     }
-    for (auto &e : ev) cudaEventDestroy(e);
     return s;
 }
 

@@ -528,6 +528,8 @@ ccgf_status build_intermediates(ccgf_handle *h, const ccgf_system *sys, cudaStre
     CCGF_TRY(dalloc(h->ksub_d, nk * nk));
     CCGF_CUDA_TRY(cudaMemcpyAsync(h->kadd_d.p, h->km.add.data(), sizeof(int) * nk * nk, cudaMemcpyHostToDevice, st));
     CCGF_CUDA_TRY(cudaMemcpyAsync(h->ksub_d.p, h->km.sub.data(), sizeof(int) * nk * nk, cudaMemcpyHostToDevice, st));
+    CCGF_TRY(dalloc(h->zero_tab, 3));
+    CCGF_CUDA_TRY(cudaMemsetAsync(h->zero_tab.p, 0, 3 * sizeof(i64), st));
     Dims D{nk, o, v, n, Q, h->kadd_d.p, h->ksub_d.p};
 
     // finite-input check (host arrays were already copied to device by the caller)

@@ -30,20 +30,50 @@ template <> struct cvec<double> { typedef double2 T; };
 template <> struct cvec<float> { typedef float2 T; };
 
 // ----------------------------------------------------------------------------- device buffers
+// Owning device buffer: freed by its destructor, so every early return of a function frees the
+// buffers it allocated; movable, not copyable.
 template <typename T> struct DBuf {
     T *p = nullptr;
     i64 n = 0;
+    DBuf() = default;
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    DBuf(DBuf &&o) noexcept : p(o.p), n(o.n) {
+        o.p = nullptr;
+        o.n = 0;
+    }
+    DBuf &operator=(DBuf &&o) noexcept {
+        if (this != &o) {
+            release();
+            p = o.p;
+            n = o.n;
+            o.p = nullptr;
+            o.n = 0;
+        }
+        return *this;
+    }
+    ~DBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
 };
 ccgf_status dalloc_bytes(void **p, size_t bytes);
 template <typename T> ccgf_status dalloc(DBuf<T> &b, i64 n) {
-    b.n = n;
-    return dalloc_bytes((void **)&b.p, (size_t)(n > 0 ? n : 1) * sizeof(T));
+    b.release();
+    ccgf_status s = dalloc_bytes((void **)&b.p, (size_t)(n > 0 ? n : 1) * sizeof(T));
+    b.n = s == CCGF_OK ? n : 0;
+    return s;
 }
-template <typename T> void dfree(DBuf<T> &b) {
-    if (b.p) cudaFree(b.p);
-    b.p = nullptr;
-    b.n = 0;
-}
+template <typename T> void dfree(DBuf<T> &b) { b.release(); }
+
+// Runs a cleanup on every exit path of a scope (pinned host memory, events).
+template <typename F> struct ScopeExit {
+    F f;
+    ~ScopeExit() { f(); }
+};
+template <typename F> ScopeExit<F> on_scope_exit(F f) { return ScopeExit<F>{f}; }
 
 // ----------------------------------------------------------------------------- batched GEMM
 // C_b = alpha * sum_{r<nred} A_{b,r} B_{b,r} + beta * C_b,  complex, b < batch.
@@ -55,6 +85,7 @@ struct GemmDesc {
     double2 alpha, beta;
     int tile;                        // SIMT per-thread tile: 0 = the launcher's model choice, k = its k-th candidate
     int ksplit;                      // SIMT split of K across CTAs: 0 = the launcher's model choice
+    unsigned long long wait_ns;      // tensor-core kernels: bound of each device wait (0 = 2 s)
 };
 int zgemm_tile_count();              // number of SIMT tile candidates
 // Long-K GEMMs with few output tiles split K across CTAs (deterministic: partial sums go to
@@ -182,6 +213,12 @@ struct ccgf_handle {
     // learned warm start (mlp.cu); capture of training solutions while ws_capturing
     WarmStart *ws = nullptr;
     bool ws_capturing = false;
+    // bound of every tensor-core device wait (from ccgf_options::device_wait_timeout_ms)
+    unsigned long long wait_ns = 1000000000ull;
+    // three zero offsets on this handle's device (single-block GEMM / permute launches)
+    DBuf<i64> zero_tab;
+    // layout transposes of ccgf_sigma_ip / ea (grown on demand, reused across calls)
+    DBuf<double2> abi_x, abi_y;
     // optional per-step timing of one sigma call (ccgf_sigma_profile)
     cudaEvent_t *prof_events = nullptr;
     int prof_max = 0, prof_count = 0;

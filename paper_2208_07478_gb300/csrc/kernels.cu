@@ -1,6 +1,7 @@
 // Generic device kernels: batched complex GEMM (FP64 / FP32 SIMT), batched strided
 // permute-add, layout transposes, plus small shared helpers of the library.
 #include "ccgf_internal.h"
+#include <atomic>
 #include <mutex>
 #include <cmath>
 
@@ -8,7 +9,21 @@ static thread_local std::string g_last_error;
 void set_last_error(const std::string &msg) { g_last_error = msg; }
 extern "C" const char *ccgf_last_error(void) { return g_last_error.c_str(); }
 
+// Host-side failure injection for the error-path tests: after `g_fail_after` more successful
+// allocations, every dalloc_bytes reports an out-of-memory error without calling cudaMalloc.
+static std::atomic<long long> g_fail_after{-1};
+extern "C" void ccgf_inject_alloc_failure(long long after) { g_fail_after.store(after); }
+
 ccgf_status dalloc_bytes(void **p, size_t bytes) {
+    long long left = g_fail_after.load();
+    while (left >= 0) {
+        if (left == 0) {
+            *p = nullptr;
+            set_last_error("cudaMalloc(" + std::to_string(bytes) + "): injected out-of-memory failure");
+            return CCGF_ERR_OOM;
+        }
+        if (g_fail_after.compare_exchange_weak(left, left - 1)) break;
+    }
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         *p = nullptr;

@@ -638,6 +638,7 @@ int run_gemm_step(ccgf_handle *h, const SigmaPlan *P, const SigmaStep &s, int ch
     const i64 *offs = P->offsets.p;
     T *C = s.c_buf == BUF_Y ? yout : scr;
     GemmDesc d = s.g;
+    d.wait_ns = h->wait_ns;
     d.offA = offs + s.offA_pos;
     d.offB = offs + s.offB_pos;
     d.offC = offs + s.offC_pos;
@@ -722,6 +723,10 @@ template <typename R>
 ccgf_status autotune_plan(ccgf_handle *h, SigmaPlan *P, int pi, bool tensor_cores, typename cvec<R>::T *scr,
                           typename cvec<R>::T *yout, cudaStream_t st) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = on_scope_exit([&] {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    });
     for (SigmaStep &s : P->steps) {
         if (s.kind != STEP_GEMM) continue;
         if (s.choice[pi] != 0) {
@@ -784,8 +789,6 @@ ccgf_status autotune_plan(ccgf_handle *h, SigmaPlan *P, int pi, bool tensor_core
         std::lock_guard<std::mutex> lk(g_tuned_mu);
         g_tuned[key] = best;
     }
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
     return CCGF_OK;
 }
 

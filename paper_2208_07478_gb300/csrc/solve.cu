@@ -333,11 +333,17 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
     ccgf_stats S{};
     double warm_rel_sum = 0, warm_net_sum = 0, warm_base_sum = 0;
     i64 warm_count = 0;
-    cudaEvent_t ev0, ev1, es0, es1;
-    cudaEventCreate(&ev0);
-    cudaEventCreate(&ev1);
-    cudaEventCreate(&es0);
-    cudaEventCreate(&es1);
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, es0 = nullptr, es1 = nullptr;
+    int *nunconv_h = nullptr;
+    auto cleanup = on_scope_exit([&] {
+        if (nunconv_h) cudaFreeHost(nunconv_h);
+        for (cudaEvent_t e : {ev0, ev1, es0, es1})
+            if (e) cudaEventDestroy(e);
+    });
+    CCGF_CUDA_TRY(cudaEventCreate(&ev0));
+    CCGF_CUDA_TRY(cudaEventCreate(&ev1));
+    CCGF_CUDA_TRY(cudaEventCreate(&es0));
+    CCGF_CUDA_TRY(cudaEventCreate(&es1));
     cudaEventRecord(ev0, st);
     const i64 launches0 = h->launches;
 
@@ -351,7 +357,6 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
     CCGF_CUDA_TRY(cudaMemsetAsync(G, 0, sizeof(double2) * Gn, st));
 
     ccgf_status final_status = CCGF_OK;
-    int *nunconv_h = nullptr;
     CCGF_CUDA_TRY(cudaMallocHost(&nunconv_h, sizeof(int)));
     double sigma_ms = 0;
 
@@ -531,13 +536,8 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                             pd.sC[0] = 1;
                             pd.total = pd.dims[0];
                             pd.batch = 1;
-                            static thread_local DBuf<i64> zero_off;
-                            if (!zero_off.p) {
-                                CCGF_TRY(dalloc(zero_off, 1));
-                                CCGF_CUDA_TRY(cudaMemset(zero_off.p, 0, sizeof(i64)));
-                            }
-                            pd.offA = zero_off.p;
-                            pd.offC = zero_off.p;
+                            pd.offA = h->zero_tab.p;
+                            pd.offC = h->zero_tab.p;
                             pd.alpha = make_double2(1, 0);
                             pd.beta = make_double2(1, 0);
                             h->launches += launch_zpermute<double>(pd, Hs2.p, Hs.p, st);
@@ -578,11 +578,6 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                 if (!converged) final_status = CCGF_NOT_CONVERGED;
                 // G contraction: Ct[q][c] = sum_mu E[q][mu] X[mu][c]
                 {
-                    static thread_local DBuf<i64> zoff;
-                    if (!zoff.p) {
-                        CCGF_TRY(dalloc(zoff, 3));
-                        CCGF_CUDA_TRY(cudaMemset(zoff.p, 0, 3 * sizeof(i64)));
-                    }
                     GemmDesc gd{};
                     gd.M = N;
                     gd.N = nv;
@@ -595,9 +590,9 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                     gd.csB = 1;
                     gd.rsC = nv;
                     gd.csC = 1;
-                    gd.offA = zoff.p;
-                    gd.offB = zoff.p + 1;
-                    gd.offC = zoff.p + 2;
+                    gd.offA = h->zero_tab.p;
+                    gd.offB = h->zero_tab.p + 1;
+                    gd.offC = h->zero_tab.p + 2;
                     gd.alpha = make_double2(1, 0);
                     gd.beta = make_double2(0, 0);
                     h->launches += launch_zgemm<double>(gd, E.p, X.p, Ct.p, st, Wk.p, Wk.n);
@@ -625,11 +620,6 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
     S.kernel_launches = h->launches - launches0;
     if (stats) *stats = S;
     dfree(Gd);
-    cudaFreeHost(nunconv_h);
-    cudaEventDestroy(ev0);
-    cudaEventDestroy(ev1);
-    cudaEventDestroy(es0);
-    cudaEventDestroy(es1);
     if (opt->prec == CCGF_TF32X3) CCGF_TRY(tc_error_check(h, st));
     return final_status;
 }

@@ -36,7 +36,9 @@ namespace {
 constexpr int BM = 128;          // rows per CTA = MMA M = TMEM lanes
 constexpr int BKC = 16;          // complex K per stage (32 real K = one 128-byte core-matrix row strip)
 constexpr int NTHREADS = 256;
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s per wait (one tile of MMAs takes microseconds)
+// Every wait is bounded by GemmDesc::wait_ns (the handle's device_wait_timeout_ms; one tile of MMAs
+// takes microseconds); kWaitLimitNs applies where a kernel has no descriptor.
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -92,6 +94,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, unsign
     return false;
 }
 
+// descriptor copy with the wait bound set (0 = the default bound)
+inline GemmDesc with_wait_limit(const GemmDesc &d) {
+    GemmDesc o = d;
+    if (o.wait_ns == 0) o.wait_ns = kWaitLimitNs;
+    return o;
+}
+
 __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t accumulate) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
@@ -141,7 +150,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_zgemm_kernel(GemmDesc d, const
 
     for (int kt = 0; kt < total; ++kt) {
         const int st = kt & 1;
-        if (kt >= 2 && !mbar_wait(&bars[st], ((kt - 2) >> 1) & 1)) {
+        if (kt >= 2 && !mbar_wait(&bars[st], ((kt - 2) >> 1) & 1, d.wait_ns)) {
             // the MMAs that read this stage two tiles ago did not finish in time
             atomicExch(err, 1);
             abort_flag = 1;
@@ -232,7 +241,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_zgemm_kernel(GemmDesc d, const
     }
     if (issued > 0) {
         const int last = issued - 1;
-        if (!mbar_wait(&bars[last & 1], (last >> 1) & 1)) {
+        if (!mbar_wait(&bars[last & 1], (last >> 1) & 1, d.wait_ns)) {
             atomicExch(err, 1);
             abort_flag = 1;
         }
@@ -284,7 +293,7 @@ template <int NCOLS>
 void launch_cols(dim3 grid, size_t smem, cudaStream_t st, const GemmDesc &d, const float2 *A, const float2 *B, float2 *C, int BNc,
                  int *err) {
     cudaFuncSetAttribute(tc_zgemm_kernel<NCOLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    tc_zgemm_kernel<NCOLS><<<grid, NTHREADS, smem, st>>>(d, A, B, C, BNc, err);
+    tc_zgemm_kernel<NCOLS><<<grid, NTHREADS, smem, st>>>(with_wait_limit(d), A, B, C, BNc, err);
 }
 
 
@@ -323,7 +332,8 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 // bounded wait that also gives up as soon as another role has aborted the CTA
-__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, unsigned parity, volatile int *abort_flag) {
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, unsigned parity, volatile int *abort_flag,
+                                                   unsigned long long limit_ns) {
     const uint32_t a = smem_u32(bar);
     const unsigned long long t0 = globaltimer_ns();
     for (unsigned it = 0; it < (1u << 30); ++it) {
@@ -334,7 +344,7 @@ __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, unsigned parit
             : "r"(a), "r"(parity)
             : "memory");
         if (done) return true;
-        if ((it & 255) == 255 && (*abort_flag || globaltimer_ns() - t0 > kWaitLimitNs)) return false;
+        if ((it & 255) == 255 && (*abort_flag || globaltimer_ns() - t0 > limit_ns)) return false;
     }
     return false;
 }
@@ -390,7 +400,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
             int issued = 0;
             for (int kt = 0; kt < total; ++kt) {
                 const int s = kt % S;
-                if (kt >= S && !mbar_wait_or_abort(&empty[s], ((kt / S) - 1) & 1, abort_v)) {
+                if (kt >= S && !mbar_wait_or_abort(&empty[s], ((kt / S) - 1) & 1, abort_v, d.wait_ns)) {
                     atomicExch(err, 1);
                     *abort_v = 1;
                     break;
@@ -405,7 +415,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
             }
             // no copy may still be writing shared memory when the CTA exits
             for (int kt = issued - S > 0 ? issued - S : 0; kt < issued; ++kt)
-                if (!mbar_wait(&fullA[kt % S], (kt / S) & 1)) atomicExch(err, 1);
+                if (!mbar_wait(&fullA[kt % S], (kt / S) & 1, d.wait_ns)) atomicExch(err, 1);
         }
     } else if (warp == 5) {
         if (lane == 0) {
@@ -415,7 +425,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
             for (int kt = 0; kt < total; ++kt) {
                 const int s = kt % S;
                 const unsigned par = (kt / S) & 1;
-                if (!mbar_wait_or_abort(&fullA[s], par, abort_v) || !mbar_wait_or_abort(&fullB[s], par, abort_v)) {
+                if (!mbar_wait_or_abort(&fullA[s], par, abort_v, d.wait_ns) || !mbar_wait_or_abort(&fullB[s], par, abort_v, d.wait_ns)) {
                     atomicExch(err, 1);
                     *abort_v = 1;
                     break;
@@ -445,7 +455,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
         const int nl = lane & 3, kp = lane >> 2;
         for (int kt = 0; kt < total; ++kt) {
             const int s = kt % S;
-            if (kt >= S && !mbar_wait_or_abort(&empty[s], ((kt / S) - 1) & 1, abort_v)) {
+            if (kt >= S && !mbar_wait_or_abort(&empty[s], ((kt / S) - 1) & 1, abort_v, d.wait_ns)) {
                 atomicExch(err, 1);
                 *abort_v = 1;
                 break;
@@ -497,7 +507,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
             if (lane == 0) mbar_arrive(&fullB[s]);
         }
         // epilogue: wait for the accumulator, then TMEM -> registers -> C
-        const bool ok = mbar_wait_or_abort(accum, 0, abort_v);
+        const bool ok = mbar_wait_or_abort(accum, 0, abort_v, d.wait_ns);
         if (!ok) atomicExch(err, 1);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (__all_sync(0xffffffffu, ok && !*abort_v)) {
@@ -539,7 +549,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
         // every MMA this CTA issued has completed once the accumulator barrier fired; after an
         // abort, wait for it (bounded) before the columns are released
         if (*abort_v) {
-            if (!mbar_wait(accum, 0)) atomicExch(err, 1);
+            if (!mbar_wait(accum, 0, d.wait_ns)) atomicExch(err, 1);
             __syncwarp();
         }
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
@@ -561,7 +571,7 @@ template <int NCOLS>
 void launch_tma_cols(dim3 grid, size_t smem, cudaStream_t st, const GemmDesc &d, const CUtensorMap &mh, const CUtensorMap &ml,
                      const i64 *rowA, const float2 *B, float2 *C, int BNc, int S, int *err) {
     cudaFuncSetAttribute(tc_zgemm_tma_kernel<NCOLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    tc_zgemm_tma_kernel<NCOLS><<<grid, TMA_THREADS, smem, st>>>(d, mh, ml, rowA, B, C, BNc, S, err);
+    tc_zgemm_tma_kernel<NCOLS><<<grid, TMA_THREADS, smem, st>>>(with_wait_limit(d), mh, ml, rowA, B, C, BNc, S, err);
 }
 
 
@@ -713,7 +723,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
             int issued = 0;
             for (int kt = 0; kt < total; ++kt) {
                 const int s = kt % S;
-                if (kt >= S && !mbar_wait_or_abort(&empty[s], ((kt / S) - 1) & 1, abort_v)) {
+                if (kt >= S && !mbar_wait_or_abort(&empty[s], ((kt / S) - 1) & 1, abort_v, d.wait_ns)) {
                     atomicExch(err, 1);
                     *abort_v = 1;
                     break;
@@ -730,7 +740,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
                 issued = kt + 1;
             }
             for (int kt = issued - S > 0 ? issued - S : 0; kt < issued; ++kt)
-                if (!mbar_wait(&full[kt % S], (kt / S) & 1)) atomicExch(err, 1);
+                if (!mbar_wait(&full[kt % S], (kt / S) & 1, d.wait_ns)) atomicExch(err, 1);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -738,7 +748,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
             int issued = 0;
             for (int kt = 0; kt < total; ++kt) {
                 const int s = kt % S;
-                if (!mbar_wait_or_abort(&full[s], (kt / S) & 1, abort_v)) {
+                if (!mbar_wait_or_abort(&full[s], (kt / S) & 1, abort_v, d.wait_ns)) {
                     atomicExch(err, 1);
                     *abort_v = 1;
                     break;
@@ -763,7 +773,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
         }
     } else {
         const int quarter = warp & 3;
-        const bool ok = mbar_wait_or_abort(accum, 0, abort_v);
+        const bool ok = mbar_wait_or_abort(accum, 0, abort_v, d.wait_ns);
         if (!ok) atomicExch(err, 1);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (__all_sync(0xffffffffu, ok && !*abort_v)) {
@@ -803,7 +813,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
     __syncthreads();
     if (warp == 1) {
         if (*abort_v) {
-            if (!mbar_wait(accum, 0)) atomicExch(err, 1);
+            if (!mbar_wait(accum, 0, d.wait_ns)) atomicExch(err, 1);
             __syncwarp();
         }
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
@@ -814,7 +824,7 @@ template <int NCOLS>
 void launch_bulk_cols(dim3 grid, size_t smem, cudaStream_t st, const GemmDesc &d, const CUtensorMap &mh, const CUtensorMap &ml,
                       const i64 *rowA, const i64 *bslot, const float *img, float2 *C, int BNc, int S, int *err) {
     cudaFuncSetAttribute(tc_zgemm_bulk_kernel<NCOLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    tc_zgemm_bulk_kernel<NCOLS><<<grid, TMA_THREADS, smem, st>>>(d, mh, ml, rowA, bslot, img, C, BNc, S, err);
+    tc_zgemm_bulk_kernel<NCOLS><<<grid, TMA_THREADS, smem, st>>>(with_wait_limit(d), mh, ml, rowA, bslot, img, C, BNc, S, err);
 }
 
 

@@ -61,3 +61,15 @@ def test_product_path_refuses_to_run_without_the_library(tmp_path):
     from paper_2208_07478_gb300 import binding
     with pytest.raises(FileNotFoundError):
         binding.load(str(tmp_path / "libccgf.so"))
+
+
+def test_wait_bound_option_is_validated(lib):
+    from paper_2208_07478_gb300 import binding as B
+    h = ctypes.c_void_p()
+    s = B.System()
+    s.kmesh[:] = [1, 1, 1]
+    for bad in (0.0, -1.0, 6.0e4 + 1.0):
+        o = B.default_options(device_wait_timeout_ms=bad)
+        assert lib.ccgf_build_intermediates(ctypes.byref(s), ctypes.byref(o), None, ctypes.byref(h)) == B.CCGF_ERR_INVALID_ARG
+        assert b"device_wait_timeout_ms" in lib.ccgf_last_error()
+    assert B.default_options().device_wait_timeout_ms == 1000.0

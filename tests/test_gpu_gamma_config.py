@@ -1,0 +1,50 @@
+"""The Gamma-point IP workload (1x1x1 mesh, nocc 4, nvir 12, Naux 48, 16 frequencies in
+[-1, 1] Ha, eta 0.01; T1 = 0, T2 the MP2 amplitudes), the nk = 1 limit of Eq. 9: all 16
+orbitals at all 16 frequencies on the GPU against the oracle's dense LU solves of the
+explicit EOM-IP matrix (dimension 196).
+  plain FP64 at tol 1e-12: |dG| <= 1e-8 per element;
+  chosen forms at tol 1e-6: |dG| <= 1e-6 max(1, |G|) per element.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2208_07478_gb300 import binding as B
+from paper_2208_07478_gb300.synth import make_workload
+from oracle.kccsd import KEOM
+from oracle import solvers
+
+
+@pytest.fixture(scope="module")
+def case():
+    s = make_workload("gamma_ip_o4v12")
+    ke = KEOM(s.kmesh, s.nocc, s.mo_energy, s.t1, s.t2, L=s.L)
+    A = ke.matrix("ip", 0)
+    n = s.nmo
+    Bm = np.stack([ke.rhs_ip(0, p) for p in range(n)], 1)
+    Em = np.stack([ke.left_ip(0, q) for q in range(n)], 0)
+    Gref = solvers.dense_gf("ip", A, Bm, Em, s.omega, s.eta)
+    h = B.build_intermediates(s.kmesh, s.nocc, s.nvir, s.naux, s.mo_energy, s.L, s.t1, s.t2)
+    yield s, h, Gref
+    h.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(B.FP64, 1e-12), (B.TF32X3, 1e-6), (B.FP32, 1e-6)],
+                         ids=["fp64", "tf32x3", "fp32"])
+def test_gamma_ip_all_orbitals_all_frequencies(case, prec, tol):
+    s, h, Gref = case
+    G = np.zeros((1, len(s.omega), s.nmo, s.nmo), dtype=np.complex128)
+    opt = B.default_options(prec=prec, tol=tol, restart_m=40, max_iter=4000, max_refine=40, omega_chunk=4)
+    st, stats = B.solve_gf(h, B.IP, s.omega, s.eta, G, options=opt)
+    assert st == B.CCGF_OK
+    assert stats["rhs_solved"] == s.nmo * len(s.omega)
+    d = np.abs(G[0] - Gref)
+    if prec == B.FP64:
+        assert d.max() <= 1e-8, d.max()
+    else:
+        assert (d / np.maximum(1.0, np.abs(Gref))).max() <= 1e-6, d.max()
