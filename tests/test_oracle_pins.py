@@ -235,3 +235,22 @@ def test_high_frequency_moment_expansion():
         v = A @ v
     exact = solvers.dense_gf("ip", A, b[:, None], e[None, :], [om], ETA)[0, 0, 0]
     assert abs(series - exact) < 1e-13
+
+
+# ---------------------------------------------------------------- element-wise oracle for large systems
+@pytest.mark.parametrize("kmesh,o,v,seed", [((2, 1, 1), 2, 3, 31), ((1, 2, 2), 1, 3, 32), ((3, 1, 1), 2, 2, 33)])
+def test_rows_oracle_equals_full_oracle(kmesh, o, v, seed):
+    """oracle.rows.KRows (per-element H_bar from the density-fitting factors) reproduces every element
+    of KEOM's sigma vectors (which forms every integral and H_bar block), both sectors, all K."""
+    from oracle.rows import KRows
+    s = make_system(kmesh, o, v, 5, seed=seed, L_sigma=0.1, t1_sigma=0.05, nomega=0)
+    ke = KEOM(s.kmesh, s.nocc, s.mo_energy, s.t1, s.t2, L=s.L)
+    kr = KRows(s.kmesh, s.nocc, s.mo_energy, s.t1, s.t2, s.L)
+    rng = np.random.default_rng(seed)
+    for K in range(s.nk):
+        for kind in ("ip", "ea"):
+            D = ke.ip_dim() if kind == "ip" else ke.ea_dim()
+            x = rng.normal(size=D) + 1j * rng.normal(size=D)
+            full = (ke.sigma_ip if kind == "ip" else ke.sigma_ea)(K, x)
+            rows = (kr.sigma_ip_elements if kind == "ip" else kr.sigma_ea_elements)(K, x, range(D))
+            np.testing.assert_allclose(rows, full, atol=1e-12 * np.abs(full).max())
