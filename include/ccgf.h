@@ -87,7 +87,8 @@ typedef struct {
     int restart_m;            /* GMRES restart length                                      */
     int max_iter;             /* cap on inner iterations per right-hand side              */
     int max_refine;           /* cap on FP64 true-residual checks (refinement cycles)      */
-    int omega_chunk;          /* frequencies solved together per (sector, K) batch         */
+    int omega_chunk;          /* frequencies solved together per (sector, K) batch (at most;
+                                 the solver splits batches that do not fit in device memory) */
     double device_wait_timeout_ms; /* bound of every tensor-core device wait, (0, 60000] ms;
                                       a wait that runs out makes the call return
                                       CCGF_ERR_TIMEOUT. Build: the handle's bound for sigma
@@ -95,6 +96,16 @@ typedef struct {
     int warm_start;           /* 1: initial vectors from the trained warm-start network
                                  (ccgf_train_warmstart), kept per column only when their true
                                  residual is below the cold start's |b|                    */
+    int kpoint;               /* solve: -1 all k-points (default), else only this total momentum
+                                 (G of the other k-points is left zero)                     */
+    int orbital_first;        /* solve: right-hand sides for orbitals [orbital_first,          */
+    int orbital_count;        /*   orbital_first + orbital_count) only (count 0: all); G keeps
+                                 IP rows p / EA columns q of those orbitals, zero elsewhere   */
+    int direct_terms;         /* build only: 0 chooses by size; 1 stores every H_bar block;
+                                 2 stores no O(nk^3 o v^3) block: the W_vvvo r1 term, the
+                                 (2<am|ef> - <am|fe>) r2 term of the EA singles and the T2 part of
+                                 the EA ladder are then formed in each sigma from the
+                                 density-fitting factors (same operator, less memory)       */
 } ccgf_options;
 
 typedef struct {
@@ -113,6 +124,11 @@ typedef struct {
     double warm_rel_residual;   /* mean |b - M x0| / |b| of the starts used (cold = 1)     */
     double warm_rel_residual_net;  /* ... of the network's prediction (0 when not used)   */
     double warm_rel_residual_base; /* ... of the baseline alone                           */
+    long long restart_used;     /* GMRES restart length used (the requested one unless device
+                                   memory made the solver shorten it, never below 10)      */
+    long long columns_per_batch;/* largest number of right-hand sides solved together: all
+                                   orbitals x omega_chunk frequencies when they fit in device
+                                   memory, else orbital chunks of equal width             */
 } ccgf_stats;
 
 typedef struct ccgf_handle ccgf_handle;

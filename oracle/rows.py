@@ -25,6 +25,7 @@ class KRows:
         self.nmo = n = mo_energy.shape[1]
         self.nvir = n - o
         self.t1, self.t2 = t1, t2
+        self._l1, self._l2 = l1, l2
         O, V = slice(0, o), slice(o, None)
         # dressing X = 1 - t, Y = 1 + t (t[a,i] = t1[i,a]) applied to the factors: L~ = X L Y
         X = np.zeros((nk, n, n), dtype=np.complex128)
@@ -289,3 +290,25 @@ class KRows:
             val -= Xe @ t[ki, kj, K][i, j, :, a]
             out.append(val)
         return np.array(out)
+
+    # ---------------------------------------------------------------- right-hand sides, left vectors
+    # b and e of Eqs. 6-7 need only the amplitudes: the KEOM methods apply as they stand.
+    @property
+    def l1(self):
+        return self.t1.conj() if self._l1 is None else self._l1
+
+    @property
+    def l2(self):
+        return self.t2.conj() if self._l2 is None else self._l2
+
+    @staticmethod
+    def pack(r1, r2):
+        return np.concatenate([r1.ravel(), r2.ravel()])
+
+    def rhs(self, kind, K, p):
+        from oracle.kccsd import KEOM
+        return (KEOM.rhs_ip if kind == "ip" else KEOM.rhs_ea)(self, K, p)
+
+    def left(self, kind, K, p):
+        from oracle.kccsd import KEOM
+        return (KEOM.left_ip if kind == "ip" else KEOM.left_ea)(self, K, p)

@@ -30,7 +30,8 @@ class System(C.Structure):
 class Options(C.Structure):
     _fields_ = [("prec", C.c_int), ("tol", C.c_double), ("restart_m", C.c_int), ("max_iter", C.c_int),
                 ("max_refine", C.c_int), ("omega_chunk", C.c_int), ("device_wait_timeout_ms", C.c_double),
-                ("warm_start", C.c_int)]
+                ("warm_start", C.c_int), ("kpoint", C.c_int), ("orbital_first", C.c_int), ("orbital_count", C.c_int),
+                ("direct_terms", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -40,7 +41,8 @@ class Stats(C.Structure):
                 ("kernel_launches", C.c_longlong), ("warm_columns", C.c_longlong), ("warm_fallbacks", C.c_longlong),
                 ("warm_val_loss", C.c_double), ("warm_val_loss_baseline", C.c_double),
                 ("warm_rel_residual", C.c_double), ("warm_rel_residual_net", C.c_double),
-                ("warm_rel_residual_base", C.c_double)]
+                ("warm_rel_residual_base", C.c_double), ("restart_used", C.c_longlong),
+                ("columns_per_batch", C.c_longlong)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -65,6 +65,10 @@ void ccgf_default_options(ccgf_options *opt) {
     opt->omega_chunk = 1;
     opt->device_wait_timeout_ms = 1000.0;
     opt->warm_start = 0;
+    opt->kpoint = -1;
+    opt->orbital_first = 0;
+    opt->orbital_count = 0;
+    opt->direct_terms = 0;
 }
 
 const char *ccgf_status_string(ccgf_status s) {
@@ -131,7 +135,7 @@ ccgf_status ccgf_build_intermediates(const ccgf_system *sys, const ccgf_options 
         conj_kernel<<<1024, 256, 0, st>>>(h->t2.p, h->l2.p, h->l2.n);
         h->launches++;
     }
-    if ((s = build_intermediates(h, sys, st)) != CCGF_OK) return fail(s);
+    if ((s = build_intermediates(h, sys, opt, st)) != CCGF_OK) return fail(s);
     *out = h;
     return CCGF_OK;
 }
@@ -205,6 +209,11 @@ ccgf_status ccgf_solve_gf(ccgf_handle *h, int sectors, int nomega, const double 
     }
     if (o.prec != CCGF_FP64 && o.prec != CCGF_FP32 && o.prec != CCGF_TF32X3) { set_last_error("unknown precision"); return CCGF_ERR_INVALID_ARG; }
     if (!valid_wait(o.device_wait_timeout_ms)) { set_last_error("device_wait_timeout_ms must be in (0, 60000]"); return CCGF_ERR_INVALID_ARG; }
+    if (o.kpoint < -1 || o.kpoint >= h->nk || o.orbital_first < 0 || o.orbital_count < 0 ||
+        o.orbital_first + o.orbital_count > h->n || (o.orbital_count == 0 && o.orbital_first != 0)) {
+        set_last_error("kpoint must be -1 or a k index; orbital_first / orbital_count must select orbitals of the cell");
+        return CCGF_ERR_INVALID_ARG;
+    }
     // the solve's own wait bound for its duration; the handle's build-time bound afterwards
     struct WaitScope {
         ccgf_handle *h;

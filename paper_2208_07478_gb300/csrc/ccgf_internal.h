@@ -88,6 +88,7 @@ struct GemmDesc {
     unsigned long long wait_ns;      // tensor-core kernels: bound of each device wait (0 = 2 s)
 };
 int zgemm_tile_count();              // number of SIMT tile candidates
+int zgemm_model_tile(const GemmDesc &d);   // 1-based candidate the launcher's model picks
 // Long-K GEMMs with few output tiles split K across CTAs (deterministic: partial sums go to
 // `work`, then one reduction applies alpha / beta); work may be NULL (no split).
 int zgemm_ksplit(const GemmDesc &d);
@@ -104,6 +105,42 @@ template <typename R>
 int launch_zgemm(const GemmDesc &d, const typename cvec<R>::T *A, const typename cvec<R>::T *B,
                  typename cvec<R>::T *C, cudaStream_t st, typename cvec<R>::T *work = nullptr, i64 work_elems = 0);
 
+// ----------------------------------------------------------------------------- tensor GEMM
+// C_b = alpha * sum_{r<nred} A_{b,r} B_{b,r} + beta * C_b where each GEMM index is a pair of tensor
+// indices: index i sits at (i / d2) * s1 + (i % d2) * s2 of its operand (tgemm.cu).
+struct IMap {
+    int d2;
+    i64 s1, s2;
+};
+IMap imap_single(i64 stride);                               // i -> i * stride
+IMap imap_pair(int inner, i64 outer_stride, i64 inner_stride);   // i -> (i / inner, i % inner)
+struct TGemm {
+    int M, N, K, nred, batch;
+    IMap am, ak, bk, bn, cm, cn;       // A[m, k], B[k, n], C[m, n]
+    const i64 *offA, *offB, *offC;     // device tables: [batch * nred], [batch * nred], [batch]
+    double2 alpha, beta;
+};
+template <typename R>
+int launch_tgemm(const TGemm &d, const typename cvec<R>::T *A, const typename cvec<R>::T *B, typename cvec<R>::T *C,
+                 cudaStream_t st);
+// FP32 arithmetic on an FP64-stored A (rounded as it is loaded): operands without an FP32 copy
+int launch_tgemm_a64(const TGemm &d, const double2 *A, const float2 *B, float2 *C, cudaStream_t st);
+struct GemmDesc;
+TGemm tgemm_of(const GemmDesc &g);
+
+// Host side of the build's tensor GEMMs: offset tables per call (kept until the caller clears
+// `keep` after a synchronisation); every access is proven in bounds on the host before a launch.
+i64 imap_span(const IMap &m, i64 dim);
+struct ccgf_handle;
+struct BuildGemm {
+    ccgf_handle *h;
+    cudaStream_t st;
+    std::vector<DBuf<i64>> keep;
+    ccgf_status run(const char *what, int M, int N, int K, int nred, IMap am, IMap ak, IMap bk, IMap bn, IMap cm, IMap cn,
+                    const double2 *A, i64 lenA, const double2 *B, i64 lenB, double2 *C, i64 lenC, const std::vector<i64> &oA,
+                    const std::vector<i64> &oB, const std::vector<i64> &oC, double alpha, double beta);
+};
+
 // ----------------------------------------------------------------------------- batched permute
 // C[offC[b] + sum_d i_d sC_d] = alpha * A[offA[b] + sum_d i_d sA_d] + beta * C[...]
 struct PermDesc {
@@ -119,6 +156,8 @@ struct PermDesc {
 // *err is set to 1 when a bounded wait gives up (C is then left unwritten by that CTA)
 bool tc_zgemm_supported(const GemmDesc &d);
 int launch_tc_zgemm(const GemmDesc &d, const float2 *A, const float2 *B, float2 *C, int *err, cudaStream_t st);
+// the register-fed kernel on an FP64-stored A (an intermediate without an FP32 copy)
+int launch_tc_zgemm_a64(const GemmDesc &d, const double2 *A, const float2 *B, float2 *C, int *err, cudaStream_t st);
 struct ccgf_handle;
 // TMA-fed variant: A = intermediate a_buf, read through tensor maps over its TF32 hi / lo copies
 // (tc_prepare); rowA[b * nred + r] = offA / rsA. Returns 0 (nothing launched) when the shape or
@@ -147,12 +186,15 @@ struct KMeshH {
 // A sigma plan is a list of launches over fixed buffers: A operands are
 // intermediates (buffer ids below), B operands always live in the scratch arena
 // (the input vector is copied there first), C operands are the output or scratch.
-enum { STEP_GEMM = 0, STEP_PERM = 1, STEP_FOV_IP = 2, STEP_FOV_EA = 3, STEP_LADDER_GATHER = 4, STEP_LADDER_SCATTER = 5 };
+enum { STEP_GEMM = 0, STEP_PERM = 1, STEP_FOV_IP = 2, STEP_FOV_EA = 3, STEP_LADDER_GATHER = 4, STEP_LADDER_SCATTER = 5,
+       STEP_TGEMM = 6 };
 struct SigmaStep {
     const char *name;
     int kind;
     GemmDesc g;
     PermDesc p;
+    TGemm tg;          // STEP_TGEMM: tensor GEMM; operands a_buf, b_buf, c_buf (intermediate, BUF_SCRATCH or BUF_Y)
+    int b_buf;
     int a_buf;         // GEMM: intermediate id (or BUF_SCRATCH); PERM: source (BUF_SCRATCH)
     int c_buf;         // BUF_Y or BUF_SCRATCH
     i64 offA_pos, offB_pos, offC_pos;   // positions in the plan's offset table
@@ -176,11 +218,18 @@ enum {
     BUF_FOO, BUF_FVV, BUF_FOV,
     BUF_WVVVV, BUF_WPLUS, BUF_WMINUS, BUF_WVVVO, BUF_WOV3, BUF_UVOVV, BUF_UOOVV_EA, BUF_T2EA,
     BUF_WOVOO, BUF_WOOOO, BUF_UOOOV, BUF_UOOVV_IP, BUF_T2IP,
+    // operands of the terms evaluated from the density-fitting factors (tensor GEMMs):
+    // dressed factors L~[k1][k2][Q][p][q], the <mn|ef> block (m e | n f)[km][ke][kn][m][e][n][f], T2
+    BUF_LD, BUF_OVOV, BUF_T2,
     NBUF
 };
 
 struct WarmStart;
 struct ccgf_handle {
+    // true: the W_vvvo r1 term, the (2<am|ef> - <am|fe>) r2 term of the EA singles and the T2 part of
+    // the EA ladder are evaluated in every sigma from the density-fitting factors instead of being
+    // stored (the memory-scalable form for large k-meshes and virtual spaces)
+    bool direct = false;
     int device;
     KMeshH km;
     int nk, o, v, n, naux;
@@ -192,6 +241,7 @@ struct ccgf_handle {
     // FP64 intermediates (GEMM-ready), FP32 copies below
     DBuf<double2> W[NBUF];
     DBuf<float2> Wf[NBUF];
+    bool fp32_done = false;   // FP32 copies decided (a block may stay FP64-only for lack of memory)
     i64 wov_seg;       // size of each of W1 | W2 | WN inside BUF_WOV3
     // pair-symmetric EA ladder: representatives per pair momentum and padded block sizes
     std::vector<int> lad_np, lad_nm;
@@ -225,7 +275,9 @@ struct ccgf_handle {
 };
 
 // build.cu
-ccgf_status build_intermediates(ccgf_handle *h, const ccgf_system *sys, cudaStream_t st);
+ccgf_status build_intermediates(ccgf_handle *h, const ccgf_system *sys, const ccgf_options *opt, cudaStream_t st);
+// sigma.cu: W_vvvo[K] (stored form) = the EA r1 -> r2 terms applied to unit vectors, for every K
+ccgf_status build_wvvvo_by_plan(ccgf_handle *h, cudaStream_t st);
 // sigma.cu
 double plan_step_flops(const ccgf_handle *h, int sector, int K, int step);   // algorithmic flops of a plan step
 int plan_step_count(const ccgf_handle *h, int sector, int K);
@@ -240,11 +292,15 @@ ccgf_status tc_error_check(ccgf_handle *h, cudaStream_t st);
 // tc_gemm.cu: the bounded-wait timeout path alone (one warp, a barrier nothing arrives on)
 void launch_wait_selftest(double limit_ms, int *err, cudaStream_t st);
 // tc_gemm.cu: TF32 hi / lo copies of every FP32 intermediate, freed by tc_free
-ccgf_status tc_prepare(ccgf_handle *h, cudaStream_t st);
+// (only for blocks with an FP32 copy, and only while `reserve` bytes of device memory stay free)
+ccgf_status tc_prepare(ccgf_handle *h, cudaStream_t st, size_t reserve);
+// sigma.cu: FP32 copies of the intermediates (large blocks only while `reserve` bytes stay free)
+ccgf_status ensure_fp32(ccgf_handle *h, cudaStream_t st, size_t reserve);
 void tc_free(ccgf_handle *h);
 ccgf_status sigma_apply_in_arena(ccgf_handle *h, int sector, int K, int nv, const double2 *x, double2 *y, double2 *arena,
                                  i64 arena_elems, i64 *offsets, i64 offsets_cap, cudaStream_t st);
 i64 sigma_arena_elems(const ccgf_handle *h, int nv);
+i64 sigma_scratch_per_column(const ccgf_handle *h);
 // vectors.cu
 ccgf_status make_rhs(ccgf_handle *h, int sector, int K, int p, double2 *out, i64 ld, cudaStream_t st);
 ccgf_status make_left(ccgf_handle *h, int sector, int K, int p, double2 *out, i64 ld, cudaStream_t st);

@@ -240,6 +240,14 @@ static TileShape pick_shape(const GemmDesc &d) {
     return best;
 }
 
+// 1-based index of the tile the launcher's model picks for d
+int zgemm_model_tile(const GemmDesc &d) {
+    const TileShape s = pick_shape(d);
+    for (int i = 0; i < zgemm_tile_count(); ++i)
+        if (kShapes[i].tm == s.tm && kShapes[i].tn == s.tn && kShapes[i].ty == s.ty) return i + 1;
+    return 0;
+}
+
 int zgemm_ksplit(const GemmDesc &d) {
     if (d.ksplit > 0) {
         // explicit split: over the momentum blocks when there are several (every split non-empty),

@@ -18,9 +18,11 @@
 // built once per (sector, K, nv) and replayed on every call; the same plan runs
 // on the FP64 intermediates or on their FP32 copies.
 #include "ccgf_internal.h"
+#include <algorithm>
 #include <atomic>
 #include <cstdlib>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <tuple>
 
@@ -87,6 +89,35 @@ struct PlanBuilder {
         }
         P->steps.push_back(s);
     }
+    // tensor GEMM (pair index maps); a_buf / b_buf: intermediate or BUF_SCRATCH, c_buf: BUF_Y or BUF_SCRATCH
+    void tgemm(int M, int N, int K, int nred, int a_buf, IMap am, IMap ak, const std::vector<i64> &oA, int b_buf, IMap bk,
+               IMap bn, const std::vector<i64> &oB, int c_buf, IMap cm, IMap cn, const std::vector<i64> &oC, double alpha,
+               double beta) {
+        SigmaStep s{};
+        s.name = cur;
+        s.kind = STEP_TGEMM;
+        s.tg.M = M;
+        s.tg.N = N;
+        s.tg.K = K;
+        s.tg.nred = nred;
+        s.tg.batch = (int)oC.size();
+        s.tg.am = am;
+        s.tg.ak = ak;
+        s.tg.bk = bk;
+        s.tg.bn = bn;
+        s.tg.cm = cm;
+        s.tg.cn = cn;
+        s.tg.alpha = make_double2(alpha, 0.0);
+        s.tg.beta = make_double2(beta, 0.0);
+        s.a_buf = a_buf;
+        s.b_buf = b_buf;
+        s.c_buf = c_buf;
+        s.offA_pos = push(oA);
+        s.offB_pos = push(oB);
+        s.offC_pos = push(oC);
+        s.rowA_pos = -1;
+        P->steps.push_back(s);
+    }
     // dims (outer..inner), source strides (scratch), destination strides
     void perm(std::vector<i64> dims, std::vector<i64> sA, const std::vector<i64> &oA, int c_buf, std::vector<i64> sC,
               const std::vector<i64> &oC, double alpha, double beta) {
@@ -118,15 +149,21 @@ struct PlanBuilder {
     }
 };
 
-enum { SEG_X = 0, SEG_R, SEG_Q, SEG_T1, SEG_T3, SEG_XT, SEG_SMALL, SEG_SPLITK, SEG_END };
+enum { SEG_X = 0, SEG_R, SEG_Q, SEG_T1, SEG_T3, SEG_XT, SEG_SMALL, SEG_D0, SEG_D1, SEG_SPLITK, SEG_END };
 
-void scratch_layout(const ccgf_handle *h, int nv, i64 seg[SEG_END + 1]) {
-    const i64 nk2 = (i64)h->nk * h->nk, o = h->o, v = h->v;
+// Scratch segments (complex elements) of a plan with nv columns. D0 / D1 hold the intermediates of
+// the EA terms formed from the density-fitting factors (sized only when a plan uses them):
+//   D0 = X0 [nk][Q][v][nv] | X1 [nk][Q][o][nv] | y2 [o][nv] | Zc [nk][Q][v][nv]
+//   D1 = Y [nk][nk][o][o][o][nv]  or  Zx [nk][nk][Q][v][nv]
+void scratch_layout(const ccgf_handle *h, int nv, i64 seg[SEG_END + 1], bool df_terms) {
+    const i64 nk = h->nk, nk2 = (i64)h->nk * h->nk, o = h->o, v = h->v, Q = h->naux;
     i64 dmax = h->dim_ip > h->dim_ea ? h->dim_ip : h->dim_ea;
     i64 r2max = nk2 * o * v * (o > v ? o : v);
+    const i64 d0 = df_terms ? (2 * nk * Q * v + nk * Q * o + o) * nv : 0;
+    const i64 d1 = df_terms ? std::max(nk2 * o * o * o, nk2 * Q * v) * nv : 0;
     // split-K partials of the launcher's own splits: at most 304 slices of an (o+v) x nv product
     // (the autotuner's wave-filling splits use a separate workspace of the handle)
-    i64 sizes[SEG_END] = {dmax * nv, r2max * nv, r2max * nv, r2max * nv, r2max * nv, r2max * nv, (o + v) * (i64)nv,
+    i64 sizes[SEG_END] = {dmax * nv, r2max * nv, r2max * nv, r2max * nv, r2max * nv, r2max * nv, (o + v) * (i64)nv, d0, d1,
                           304 * (o + v) * (i64)nv};
     i64 pos = 0;
     for (int s = 0; s < SEG_END; ++s) {
@@ -136,14 +173,193 @@ void scratch_layout(const ccgf_handle *h, int nv, i64 seg[SEG_END + 1]) {
     seg[SEG_END] = pos;
 }
 
-SigmaPlan *build_plan_ea(const ccgf_handle *h, int K, int nv) {
+// offsets of the pieces of segment D0 (see scratch_layout)
+struct D0Parts {
+    i64 x0, x1, y2, zc;
+};
+D0Parts d0_parts(const ccgf_handle *h, const SigmaPlan *P) {
+    const i64 nk = h->nk, o = h->o, v = h->v, Q = h->naux, NV = P->nv, b = P->seg[SEG_D0];
+    return D0Parts{b, b + nk * Q * v * NV, b + nk * Q * v * NV + nk * Q * o * NV, b + nk * Q * v * NV + nk * Q * o * NV + o * NV};
+}
+
+// The EA r1 -> r2 coupling, sum_e W_vvvo[ka,kb,K][a,b,e,j] r1[e], evaluated from the density-fitting
+// factors (e at K, kb = K + kj - ka); W_vvvo = <ab|ej> + sum <mn|ej> t_mn^ab - sum Fov[me] t_mj^ab
+//   - sum <mb|ef> t_mj^af + sum (2<ma|fe> - <ma|ef>) t_mj^fb - sum <ma|fe> t_mj^bf, with <pq|rs> = (pr|qs):
+//   X0[ka][Q][a] = sum_e L~[ka,K,Q][a,e] r_e,  X1[km][Q][m] = sum_e L~[km,K,Q][m,e] r_e,  y2[m] = Fov[K] r
+//   T0  s2 += sum_Q X0[ka][Q][a] L~[kb,kj,Q][b,j]                                     (first write of s2)
+//   T1  Y[kj][km][m,n,j] = sum_Q X1[km][Q][m] L~[kn,kj,Q][n,j]  (kn = K + kj - km)
+//       s2 += sum_{km,m,n} t[km,kn,ka][m,n,a,b] Y[kj][km][m,n,j]    (after `extra_y` adds to Y)
+//   T2  s2 -= sum_m t[K,kj,ka][m,j,a,b] y2[m]
+//   T3  Y3[km][kb][m,b,f] = sum_Q X1[km][Q][m] L~[kb,kf,Q][b,f]  (kf = km + kb - K)
+//       s2 -= sum_{km,m,f} t[km,kj,ka][m,j,a,f] Y3[km][kb][m,b,f]
+//   T4  ZA[km][ka][m,a,f] = sum_Q L~[km,kf,Q][m,f] X0[ka][Q][a],  ZB = 2 ZA - sum_Q X1[km][Q][m] L~[ka,kf,Q][a,f]
+//       (kf = km + ka - K);  s2 += sum_{km,m,f} ZB[km][ka][m,a,f] t[km,kj,kf][m,j,f,b]
+//   T5  s2 -= sum_{km,m,f} ZA[km][ka][m,a,f] t[km,kj,kb][m,j,b,f]
+template <typename Extra>
+void emit_ea_r1_terms(PlanBuilder &B, const ccgf_handle *h, SigmaPlan *P, int K, Extra extra_y) {
+    const auto &km = h->km;
+    const int nk = h->nk, o = h->o, v = h->v, n = h->n, Q = h->naux;
+    const i64 NV = P->nv, S2 = (i64)o * v * v, v2 = (i64)v * v, o2 = (i64)o * o, n2 = (i64)n * n;
+    const i64 sx = P->seg[SEG_X];
+    const D0Parts d0 = d0_parts(h, P);
+    auto row = [&](int kj, int ka) -> i64 { return v + ((i64)kj * nk + ka) * S2; };
+    auto LB = [&](int k1, int k2) -> i64 { return ((i64)k1 * nk + k2) * Q * n2; };
+    auto TB = [&](int ki, int kj, int ka) -> i64 { return (((i64)ki * nk + kj) * nk + ka) * o2 * v2; };
+    const IMap one = imap_single(1);
+    B.cur = "ea_s2_r1_df";
+    {
+        std::vector<i64> a0, a1, bx, c0, c1;
+        for (int k = 0; k < nk; ++k) {
+            a0.push_back(LB(k, K) + (i64)o * n + o);
+            a1.push_back(LB(k, K) + o);
+            bx.push_back(sx);
+            c0.push_back(d0.x0 + (i64)k * Q * v * NV);
+            c1.push_back(d0.x1 + (i64)k * Q * o * NV);
+        }
+        // X0: rows (Q, a), X1: rows (Q, m); contraction e; columns = the nv vectors
+        B.tgemm(Q * v, (int)NV, v, 1, BUF_LD, imap_pair(v, n2, n), one, a0, BUF_SCRATCH, imap_single(NV), one, bx, BUF_SCRATCH,
+                imap_single(NV), one, c0, 1.0, 0.0);
+        B.tgemm(Q * o, (int)NV, v, 1, BUF_LD, imap_pair(o, n2, n), one, a1, BUF_SCRATCH, imap_single(NV), one, bx, BUF_SCRATCH,
+                imap_single(NV), one, c1, 1.0, 0.0);
+        B.gemm(o, (int)NV, v, 1, BUF_FOV, v, 1, {(i64)K * o * v}, NV, 1, {sx}, BUF_SCRATCH, NV, 1, {d0.y2}, 1.0, 0.0);
+    }
+    // T0 (first write of every s2 block): rows (a, c), columns (b, j), contraction Q
+    {
+        std::vector<i64> oA, oB, oC;
+        for (int kj = 0; kj < nk; ++kj)
+            for (int ka = 0; ka < nk; ++ka) {
+                const int kb = km.c(K, ka, kj);
+                oA.push_back(d0.x0 + (i64)ka * Q * v * NV);
+                oB.push_back(LB(kb, kj) + (i64)o * n);
+                oC.push_back(row(kj, ka) * NV);
+            }
+        B.tgemm(v * (int)NV, v * o, Q, 1, BUF_SCRATCH, imap_single(1), imap_single(v * NV), oA, BUF_LD, imap_single(n2),
+                imap_pair(o, n, 1), oB, BUF_Y, imap_pair((int)NV, v * NV, 1), imap_pair(o, NV, v2 * NV), oC, 1.0, 0.0);
+    }
+    // T1: Y[kj][km][m][n][j][c] in D1, rows (m, c), columns (n, j), contraction Q
+    {
+        std::vector<i64> oA, oB, oC;
+        for (int kj = 0; kj < nk; ++kj)
+            for (int kmm = 0; kmm < nk; ++kmm) {
+                const int kn = km.c(K, kmm, kj);
+                oA.push_back(d0.x1 + (i64)kmm * Q * o * NV);
+                oB.push_back(LB(kn, kj));
+                oC.push_back(P->seg[SEG_D1] + ((i64)kj * nk + kmm) * o2 * o * NV);
+            }
+        B.tgemm(o * (int)NV, (int)o2, Q, 1, BUF_SCRATCH, imap_single(1), imap_single(o * NV), oA, BUF_LD, imap_single(n2),
+                imap_pair(o, n, 1), oB, BUF_SCRATCH, imap_pair((int)NV, o2 * NV, 1), imap_pair(o, o * NV, NV), oC, 1.0, 0.0);
+    }
+    extra_y();
+    // s2 += sum_{km,m,n} t[km,kn,ka][m,n,a,b] Y[kj][km][m,n,j]: rows (a, b), columns (j, c), contraction (m, n)
+    {
+        std::vector<i64> oA, oB, oC;
+        for (int kj = 0; kj < nk; ++kj)
+            for (int ka = 0; ka < nk; ++ka) {
+                for (int kmm = 0; kmm < nk; ++kmm) {
+                    const int kn = km.c(K, kmm, kj);
+                    oA.push_back(TB(kmm, kn, ka));
+                    oB.push_back(P->seg[SEG_D1] + ((i64)kj * nk + kmm) * o2 * o * NV);
+                }
+                oC.push_back(row(kj, ka) * NV);
+            }
+        B.tgemm((int)v2, o * (int)NV, (int)o2, nk, BUF_T2, one, imap_pair(o, o * v2, v2), oA, BUF_SCRATCH,
+                imap_pair(o, o2 * NV, o * NV), imap_pair((int)NV, NV, 1), oB, BUF_Y, imap_single(NV), imap_pair((int)NV, v2 * NV, 1),
+                oC, 1.0, 1.0);
+    }
+    // T2: s2 -= t[K,kj,ka][m,j,a,b] y2[m]
+    {
+        std::vector<i64> oA, oB, oC;
+        for (int kj = 0; kj < nk; ++kj)
+            for (int ka = 0; ka < nk; ++ka) {
+                oA.push_back((((i64)K * nk + kj) * nk + ka) * S2 * o);
+                oB.push_back(d0.y2);
+                oC.push_back(row(kj, ka) * NV);
+            }
+        B.gemm((int)S2, (int)NV, o, 1, BUF_T2EA, o, 1, oA, NV, 1, oB, BUF_Y, NV, 1, oC, -1.0, 1.0);
+    }
+    // T3: Y3[km][kb][m][b][f][c] in R, rows (m, c), columns (b, f), contraction Q
+    {
+        std::vector<i64> oA, oB, oC;
+        for (int kmm = 0; kmm < nk; ++kmm)
+            for (int kb = 0; kb < nk; ++kb) {
+                const int kf = km.c(kmm, K, kb);
+                oA.push_back(d0.x1 + (i64)kmm * Q * o * NV);
+                oB.push_back(LB(kb, kf) + (i64)o * n + o);
+                oC.push_back(P->seg[SEG_R] + ((i64)kmm * nk + kb) * S2 * NV);
+            }
+        B.tgemm(o * (int)NV, (int)v2, Q, 1, BUF_SCRATCH, imap_single(1), imap_single(o * NV), oA, BUF_LD, imap_single(n2),
+                imap_pair(v, n, 1), oB, BUF_SCRATCH, imap_pair((int)NV, v2 * NV, 1), imap_pair(v, v * NV, NV), oC, 1.0, 0.0);
+    }
+    // s2 -= sum_{km,m,f} t[km,kj,ka][m,j,a,f] Y3[km][kb][m,b,f]: rows (j, a), columns (b, c), contraction (m, f)
+    {
+        std::vector<i64> oA, oB, oC;
+        for (int kj = 0; kj < nk; ++kj)
+            for (int ka = 0; ka < nk; ++ka) {
+                const int kb = km.c(K, ka, kj);
+                for (int kmm = 0; kmm < nk; ++kmm) {
+                    oA.push_back(TB(kmm, kj, ka));
+                    oB.push_back(P->seg[SEG_R] + ((i64)kmm * nk + kb) * S2 * NV);
+                }
+                oC.push_back(row(kj, ka) * NV);
+            }
+        B.tgemm(o * v, v * (int)NV, o * v, nk, BUF_T2, imap_pair(v, v2, v), imap_pair(v, o * v2, 1), oA, BUF_SCRATCH,
+                imap_pair(v, v2 * NV, NV), imap_pair((int)NV, v * NV, 1), oB, BUF_Y, imap_pair(v, v2 * NV, v * NV),
+                imap_pair((int)NV, NV, 1), oC, -1.0, 1.0);
+    }
+    // T4 / T5: ZA[km][ka][m][a][f][c] in Q, ZB = 2 ZA - (X1 . L~) in T1; rows (m, f) or (m, c)
+    {
+        std::vector<i64> aL, bX, cA, cB, aX, bL;
+        for (int kmm = 0; kmm < nk; ++kmm)
+            for (int ka = 0; ka < nk; ++ka) {
+                const int kf = km.c(kmm, K, ka);
+                aL.push_back(LB(kmm, kf) + o);
+                bX.push_back(d0.x0 + (i64)ka * Q * v * NV);
+                cA.push_back(P->seg[SEG_Q] + ((i64)kmm * nk + ka) * S2 * NV);
+                cB.push_back(P->seg[SEG_T1] + ((i64)kmm * nk + ka) * S2 * NV);
+                aX.push_back(d0.x1 + (i64)kmm * Q * o * NV);
+                bL.push_back(LB(ka, kf) + (i64)o * n + o);
+            }
+        const IMap cm_mf = imap_pair(v, v2 * NV, NV), cn_ac = imap_pair((int)NV, v * NV, 1);
+        B.tgemm(o * v, v * (int)NV, Q, 1, BUF_LD, imap_pair(v, n, 1), imap_single(n2), aL, BUF_SCRATCH, imap_single(v * NV),
+                imap_single(1), bX, BUF_SCRATCH, cm_mf, cn_ac, cA, 1.0, 0.0);
+        B.tgemm(o * v, v * (int)NV, Q, 1, BUF_LD, imap_pair(v, n, 1), imap_single(n2), aL, BUF_SCRATCH, imap_single(v * NV),
+                imap_single(1), bX, BUF_SCRATCH, cm_mf, cn_ac, cB, 2.0, 0.0);
+        // - sum_Q X1[km][Q][m][c] L~[ka,kf,Q][a,f]: rows (m, c), columns (a, f)
+        B.tgemm(o * (int)NV, (int)v2, Q, 1, BUF_SCRATCH, imap_single(1), imap_single(o * NV), aX, BUF_LD, imap_single(n2),
+                imap_pair(v, n, 1), bL, BUF_SCRATCH, imap_pair((int)NV, v2 * NV, 1), imap_pair(v, v * NV, NV), cB, -1.0, 1.0);
+    }
+    {
+        std::vector<i64> a4, a5, bB, bA, oC;
+        for (int kj = 0; kj < nk; ++kj)
+            for (int ka = 0; ka < nk; ++ka) {
+                const int kb = km.c(K, ka, kj);
+                for (int kmm = 0; kmm < nk; ++kmm) {
+                    const int kf = km.c(kmm, K, ka);
+                    a4.push_back(TB(kmm, kj, kf));   // t[km,kj,kf][m,j,f,b]
+                    a5.push_back(TB(kmm, kj, kb));   // t[km,kj,kb][m,j,b,f]
+                    bB.push_back(P->seg[SEG_T1] + ((i64)kmm * nk + ka) * S2 * NV);
+                    bA.push_back(P->seg[SEG_Q] + ((i64)kmm * nk + ka) * S2 * NV);
+                }
+                oC.push_back(row(kj, ka) * NV);
+            }
+        // rows (j, b), columns (a, c), contraction (m, f)
+        const IMap bk_mf = imap_pair(v, v2 * NV, NV), bn_ac = imap_pair((int)NV, v * NV, 1);
+        const IMap cm_jb = imap_pair(v, v2 * NV, NV), cn_ac = imap_pair((int)NV, v * NV, 1);
+        B.tgemm(o * v, v * (int)NV, o * v, nk, BUF_T2, imap_pair(v, v2, 1), imap_pair(v, o * v2, v), a4, BUF_SCRATCH, bk_mf, bn_ac,
+                bB, BUF_Y, cm_jb, cn_ac, oC, 1.0, 1.0);
+        B.tgemm(o * v, v * (int)NV, o * v, nk, BUF_T2, imap_pair(v, v2, v), imap_pair(v, o * v2, 1), a5, BUF_SCRATCH, bk_mf, bn_ac,
+                bA, BUF_Y, cm_jb, cn_ac, oC, -1.0, 1.0);
+    }
+}
+
+SigmaPlan *build_plan_ea(const ccgf_handle *h, int K, int nv, bool r1_only = false) {
     const auto &km = h->km;
     const int nk = h->nk, o = h->o, v = h->v;
     SigmaPlan *P = new SigmaPlan();
     P->sector = CCGF_SECTOR_EA;
     P->K = K;
     P->nv = nv;
-    scratch_layout(h, nv, P->seg);
+    scratch_layout(h, nv, P->seg, h->direct || r1_only);
     P->scratch_elems = P->seg[SEG_END];
     PlanBuilder B{P, {}};
     const i64 S2 = (i64)o * v * v, NV = nv;
@@ -151,26 +367,89 @@ SigmaPlan *build_plan_ea(const ccgf_handle *h, int K, int nv) {
     auto row = [&](int kj, int ka) -> i64 { return v + ((i64)kj * nk + ka) * S2; };
     const i64 v2 = (i64)v * v, ov = (i64)o * v, nk2 = (i64)nk * nk;
 
+    const int n = h->n, Q = h->naux;
+    const i64 n2 = (i64)n * n, o2 = (i64)o * o;
+    auto LB = [&](int k1, int k2) -> i64 { return ((i64)k1 * nk + k2) * Q * n2; };
+    if (r1_only) {
+        // the r1 -> r2 coupling alone (applied to unit vectors it gives the stored W_vvvo[K])
+        emit_ea_r1_terms(B, h, P, K, [] {});
+        P->host_off = B.off;
+        return P;
+    }
+
     // s1[a] = Fvv[K] r1 (first write)
     B.cur = "ea_s1_fvv";
     B.gemm(v, nv, v, 1, BUF_FVV, v, 1, {(i64)K * v2}, NV, 1, {sx}, BUF_Y, NV, 1, {0}, 1.0, 0.0);
     B.fov(STEP_FOV_EA);
-    // s1 += sum (2<am|ef> - <am|fe>) r2
+    // s1 += sum (2<am|ef> - <am|fe>) r2[km,ke][m,e,f],  <a K m km|e ke f kf> = (a e|m f), kf = K + km - ke
     B.cur = "ea_s1_vovv";
-    B.gemm(v, nv, (int)(nk2 * o * v2), 1, BUF_UVOVV, nk2 * o * v2, 1, {(i64)K * v * nk2 * o * v2}, NV, 1, {sx + v * NV},
-           BUF_Y, NV, 1, {0}, 1.0, 1.0);
+    if (!h->direct) {
+        B.gemm(v, nv, (int)(nk2 * o * v2), 1, BUF_UVOVV, nk2 * o * v2, 1, {(i64)K * v * nk2 * o * v2}, NV, 1, {sx + v * NV},
+               BUF_Y, NV, 1, {0}, 1.0, 1.0);
+    } else {
+        // Coulomb: Zc[ke][Q][e] = sum_{km,m,f} L~[km,kf,Q][m,f] r2[km,ke][m,e,f];  s1 += 2 sum L~[K,ke,Q][a,e] Zc[ke][Q][e]
+        // exchange: Zx[km][ke][Q][f] = sum_{m,e} L~[km,ke,Q][m,e] r2[km,ke][m,e,f];  s1 -= sum L~[K,kf,Q][a,f] Zx[km][ke][Q][f]
+        const D0Parts d0 = d0_parts(h, P);
+        std::vector<i64> zA, zB, zC, sA, sB, xA, xB, xC, tA, tB;
+        for (int ke = 0; ke < nk; ++ke) {
+            for (int kmm = 0; kmm < nk; ++kmm) {
+                const int kf = km.c(K, ke, kmm);
+                zA.push_back(LB(kmm, kf) + o);
+                zB.push_back(sx + row(kmm, ke) * NV);
+            }
+            zC.push_back(d0.zc + (i64)ke * Q * v * NV);
+            sA.push_back(LB(K, ke) + (i64)o * n + o);
+            sB.push_back(d0.zc + (i64)ke * Q * v * NV);
+        }
+        for (int kmm = 0; kmm < nk; ++kmm)
+            for (int ke = 0; ke < nk; ++ke) {
+                const int kf = km.c(K, ke, kmm);
+                xA.push_back(LB(kmm, ke) + o);
+                xB.push_back(sx + row(kmm, ke) * NV);
+                xC.push_back(P->seg[SEG_D1] + ((i64)kmm * nk + ke) * Q * v * NV);
+                tA.push_back(LB(K, kf) + (i64)o * n + o);
+                tB.push_back(P->seg[SEG_D1] + ((i64)kmm * nk + ke) * Q * v * NV);
+            }
+        // Zc: rows Q, columns (e, c), contraction (m, f) over km
+        B.tgemm(Q, v * nv, (int)ov, nk, BUF_LD, imap_single(n2), imap_pair(v, n, 1), zA, BUF_SCRATCH, imap_pair(v, v2 * NV, NV),
+                imap_pair(nv, v * NV, 1), zB, BUF_SCRATCH, imap_single(v * NV), imap_single(1), zC, 1.0, 0.0);
+        // s1 += 2 sum_{ke} L~[K,ke][a,(Q,e)] Zc[ke][(Q,e)][c]
+        B.tgemm(v, nv, Q * v, nk, BUF_LD, imap_single(n), imap_pair(v, n2, 1), sA, BUF_SCRATCH, imap_pair(v, v * NV, NV),
+                imap_single(1), sB, BUF_Y, imap_single(NV), imap_single(1), {0}, 2.0, 1.0);
+        // Zx: rows Q, columns (f, c), contraction (m, e)
+        B.tgemm(Q, v * nv, (int)ov, 1, BUF_LD, imap_single(n2), imap_pair(v, n, 1), xA, BUF_SCRATCH, imap_pair(v, v2 * NV, v * NV),
+                imap_single(1), xB, BUF_SCRATCH, imap_single(v * NV), imap_single(1), xC, 1.0, 0.0);
+        // s1 -= sum_{km,ke} L~[K,kf][a,(Q,f)] Zx[km][ke][(Q,f)][c]
+        B.tgemm(v, nv, Q * v, nk * nk, BUF_LD, imap_single(n), imap_pair(v, n2, 1), tA, BUF_SCRATCH, imap_pair(v, v * NV, NV),
+                imap_single(1), tB, BUF_Y, imap_single(NV), imap_single(1), {0}, -1.0, 1.0);
+    }
     // s2 = Wvvvo r1 (first write of every block)
     B.cur = "ea_s2_wvvvo";
-    {
-        std::vector<i64> oA, oB, oC;
-        for (int kj = 0; kj < nk; ++kj)
-            for (int ka = 0; ka < nk; ++ka) {
-                int kb = km.c(K, ka, kj);
-                oA.push_back((((i64)ka * nk + kb) * nk + K) * (o * v2 * v));
-                oB.push_back(sx);
-                oC.push_back(row(kj, ka) * NV);
-            }
-        B.gemm((int)(o * v2), nv, v, 1, BUF_WVVVO, v, 1, oA, NV, 1, oB, BUF_Y, NV, 1, oC, 1.0, 0.0);
+    if (!h->direct) {
+        // stored W_vvvo[K] as rows (kj, ka, j, a, b) of the r2 part, columns e
+        B.gemm((int)(nk2 * o * v2), nv, v, 1, BUF_WVVVO, v, 1, {(i64)K * nk2 * o * v2 * v}, NV, 1, {sx}, BUF_Y, NV, 1, {v * NV},
+               1.0, 0.0);
+    } else {
+        // from the density-fitting factors; the T2 part of the ladder, sum_{ke,e,f} <mn|ef> r2[kj,ke][j,e,f]
+        // = sum (m e|n f) r2 (kn = K + kj - km), joins the Y of the T1 term (both are contracted with t[km,kn,ka])
+        emit_ea_r1_terms(B, h, P, K, [&] {
+            B.cur = "ea_ladder_t2_df";
+            std::vector<i64> oA, oB, oC;
+            for (int kj = 0; kj < nk; ++kj)
+                for (int kmm = 0; kmm < nk; ++kmm) {
+                    const int kn = km.c(K, kmm, kj);
+                    for (int ke = 0; ke < nk; ++ke) {
+                        oA.push_back((((i64)kmm * nk + ke) * nk + kn) * o2 * v2);
+                        oB.push_back(sx + row(kj, ke) * NV);
+                    }
+                    oC.push_back(P->seg[SEG_D1] + ((i64)kj * nk + kmm) * o2 * o * NV);
+                }
+            // rows (m, n), columns (j, c), contraction (e, f)
+            B.tgemm((int)o2, o * nv, (int)v2, nk, BUF_OVOV, imap_pair(o, v * o * v, v), imap_pair(v, ov, 1), oA, BUF_SCRATCH,
+                    imap_pair(v, v * NV, NV), imap_pair(nv, v2 * NV, 1), oB, BUF_SCRATCH, imap_pair(o, o2 * NV, o * NV),
+                    imap_pair(nv, NV, 1), oC, 1.0, 1.0);
+            B.cur = "ea_s2_r1_df";
+        });
     }
     // s2 += Fvv[ka](a,e) r2[j,e,b]
     B.cur = "ea_s2_fvv_a";
@@ -324,7 +603,7 @@ SigmaPlan *build_plan_ip(const ccgf_handle *h, int K, int nv) {
     P->sector = CCGF_SECTOR_IP;
     P->K = K;
     P->nv = nv;
-    scratch_layout(h, nv, P->seg);
+    scratch_layout(h, nv, P->seg, false);
     P->scratch_elems = P->seg[SEG_END];
     PlanBuilder B{P, {}};
     const i64 S2 = (i64)o * o * v, NV = nv;
@@ -643,6 +922,13 @@ int run_gemm_step(ccgf_handle *h, const SigmaPlan *P, const SigmaStep &s, int ch
     d.offB = offs + s.offB_pos;
     d.offC = offs + s.offC_pos;
     const T *A = f64 ? (const T *)h->W[s.a_buf].p : (const T *)h->Wf[s.a_buf].p;
+    if constexpr (sizeof(R) == 4) {
+        if (!A) {
+            // no FP32 copy of this block (device memory): FP32 / TF32 arithmetic on the FP64 block
+            if (tensor_cores && tc_zgemm_supported(d)) return launch_tc_zgemm_a64(d, h->W[s.a_buf].p, scr, C, h->tc_err.p, st);
+            return launch_tgemm_a64(tgemm_of(d), h->W[s.a_buf].p, scr, C, st);
+        }
+    }
     if (choice == CHOICE_SMALLM) return launch_zgemm_smallm<R>(d, A, scr, C, st);
     if constexpr (sizeof(R) == 4) {
         if (tensor_cores && tc_zgemm_supported(d) && (choice == 0 || (choice >= CHOICE_TC_TMA && choice < CHOICE_SMALLM))) {
@@ -729,6 +1015,7 @@ ccgf_status autotune_plan(ccgf_handle *h, SigmaPlan *P, int pi, bool tensor_core
     });
     for (SigmaStep &s : P->steps) {
         if (s.kind != STEP_GEMM) continue;
+        if (sizeof(R) == 4 && !h->Wf[s.a_buf].p) continue;   // converted on load: one kernel per precision
         if (s.choice[pi] != 0) {
             CCGF_TRY(ensure_split_ws<R>(h, s.g, s.choice[pi], st));
             continue;
@@ -749,35 +1036,54 @@ ccgf_status autotune_plan(ccgf_handle *h, SigmaPlan *P, int pi, bool tensor_core
             CCGF_CUDA_TRY(cudaEventCreate(&e0));
             CCGF_CUDA_TRY(cudaEventCreate(&e1));
         }
+        // candidates, most promising first (the tensor-core kernels, then the launcher's own SIMT pick);
+        // a contraction whose runs are long is tuned only until 1.5 s of timing has been spent
         std::vector<int> cand;
-        for (int t = 1; t <= zgemm_tile_count(); ++t) {
-            cand.push_back(t);
-            const int ks = zgemm_wave_split(g, t);
-            if (ks > 1) cand.push_back(t + CHOICE_SPLIT * ks);
-        }
-        if (zgemm_smallm_supported(g)) cand.push_back(CHOICE_SMALLM);
-        if (sizeof(R) == 4 && tensor_cores && tc_zgemm_supported(g)) {
-            cand.push_back(CHOICE_TC_REG);
+        const bool tc_ok = sizeof(R) == 4 && tensor_cores && tc_zgemm_supported(g);
+        if (tc_ok) {
             if (s.rowA_pos >= 0) {
-                cand.push_back(CHOICE_TC_TMA);
                 cand.push_back(CHOICE_TC_BULK);
+                cand.push_back(CHOICE_TC_TMA);
+            }
+            cand.push_back(CHOICE_TC_REG);
+        }
+        {
+            GemmDesc gm = g;
+            gm.tile = 0;
+            gm.ksplit = 0;
+            const int model = zgemm_model_tile(gm);
+            if (model > 0) cand.push_back(model);
+            for (int t = 1; t <= zgemm_tile_count(); ++t) {
+                if (t != model) cand.push_back(t);
+                const int ks = zgemm_wave_split(g, t);
+                if (ks > 1) cand.push_back(t + CHOICE_SPLIT * ks);
             }
         }
+        if (zgemm_smallm_supported(g)) cand.push_back(CHOICE_SMALLM);
         int best = 0;
-        float best_ms = 1e30f;
+        float best_ms = 1e30f, spent = 0.f;
         for (int c : cand) {
+            if (spent > 1500.f && best != 0) break;
             CCGF_TRY(ensure_split_ws<R>(h, s.g, c, st));
+            CCGF_CUDA_TRY(cudaEventRecord(e0, st));
             int n = run_gemm_step<R>(h, P, s, c, tensor_cores, scr, yout, st);
+            CCGF_CUDA_TRY(cudaEventRecord(e1, st));
             if (n == 0) continue;
             h->launches += n;
+            CCGF_CUDA_TRY(cudaEventSynchronize(e1));
+            float first = 0.f;
+            CCGF_CUDA_TRY(cudaEventElapsedTime(&first, e0, e1));
+            spent += first;
             float ms = 1e30f;
-            for (int rep = 0; rep < 2; ++rep) {
+            const int reps = first > 20.f ? 1 : 2;
+            for (int rep = 0; rep < reps; ++rep) {
                 CCGF_CUDA_TRY(cudaEventRecord(e0, st));
                 h->launches += run_gemm_step<R>(h, P, s, c, tensor_cores, scr, yout, st);
                 CCGF_CUDA_TRY(cudaEventRecord(e1, st));
                 CCGF_CUDA_TRY(cudaEventSynchronize(e1));
                 float t = 0.f;
                 CCGF_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+                spent += t;
                 ms = t < ms ? t : ms;
             }
             if (ms < best_ms) {
@@ -813,6 +1119,17 @@ void run_plan(ccgf_handle *h, SigmaPlan *P, const double2 *x, double2 *y, cudaSt
         T *C = s.c_buf == BUF_Y ? yout : scr;
         if (s.kind == STEP_GEMM) {
             h->launches += run_gemm_step<R>(h, P, s, s.choice[pi], tensor_cores, scr, yout, st);
+        } else if (s.kind == STEP_TGEMM) {
+            auto ptr = [&](int b) -> T * {
+                if (b == BUF_Y) return yout;
+                if (b == BUF_SCRATCH) return scr;
+                return f64 ? (T *)h->W[b].p : (T *)h->Wf[b].p;
+            };
+            TGemm d = s.tg;
+            d.offA = offs + s.offA_pos;
+            d.offB = offs + s.offB_pos;
+            d.offC = offs + s.offC_pos;
+            h->launches += launch_tgemm<R>(d, ptr(s.a_buf), ptr(s.b_buf), ptr(s.c_buf), st);
         } else if (s.kind == STEP_PERM) {
             PermDesc d = s.p;
             d.offA = offs + s.offA_pos;
@@ -870,6 +1187,22 @@ bool check_plan(const ccgf_handle *h, const SigmaPlan *P, const std::vector<i64>
                 i64 oc = off[s.offC_pos + b];
                 if (oc < 0 || oc + spanC >= clen) { why = "gemm C out of range at step " + std::to_string(si); return false; }
             }
+        } else if (s.kind == STEP_TGEMM) {
+            const TGemm &g = s.tg;
+            auto len = [&](int b) -> i64 { return b == BUF_Y ? ylen : (b == BUF_SCRATCH ? slen : h->W[b].n); };
+            const i64 la = len(s.a_buf), lb = len(s.b_buf), lc = len(s.c_buf);
+            const i64 spanA = imap_span(g.am, g.M) + imap_span(g.ak, g.K), spanB = imap_span(g.bk, g.K) + imap_span(g.bn, g.N),
+                      spanC = imap_span(g.cm, g.M) + imap_span(g.cn, g.N);
+            if (s.b_buf != BUF_SCRATCH && s.b_buf < BUF_FOO) { why = "tensor GEMM B operand at step " + std::to_string(si); return false; }
+            for (int b = 0; b < g.batch; ++b) {
+                for (int r = 0; r < g.nred; ++r) {
+                    i64 oa = off[s.offA_pos + (i64)b * g.nred + r], ob = off[s.offB_pos + (i64)b * g.nred + r];
+                    if (oa < 0 || oa + spanA >= la) { why = "tensor GEMM A out of range at step " + std::to_string(si); return false; }
+                    if (ob < 0 || ob + spanB >= lb) { why = "tensor GEMM B out of range at step " + std::to_string(si); return false; }
+                }
+                i64 oc = off[s.offC_pos + b];
+                if (oc < 0 || oc + spanC >= lc) { why = "tensor GEMM C out of range at step " + std::to_string(si); return false; }
+            }
         } else if (s.kind == STEP_LADDER_GATHER || s.kind == STEP_LADDER_SCATTER) {
             // segments: R+/S+ need nk Pp nocc nv, R-/S- need nk Pm nocc nv elements; x2 / y2 indices
             // come from representatives of the pair space, all inside [nvir, dim_ea) rows
@@ -903,6 +1236,7 @@ bool check_plan(const ccgf_handle *h, const SigmaPlan *P, const std::vector<i64>
 
 }  // namespace
 
+
 static const SigmaPlan *plan_of(const ccgf_handle *h, int sector, int K) {
     if (h->plans.empty() || K < 0 || K >= h->nk || (sector != 1 && sector != 2)) return nullptr;
     return h->plans[(sector - 1) * h->nk + K];
@@ -916,6 +1250,7 @@ double plan_step_flops(const ccgf_handle *h, int sector, int K, int step) {
     if (!P || step < 0 || step >= (int)P->steps.size()) return 0.0;
     const SigmaStep &s = P->steps[step];
     if (s.kind == STEP_GEMM) return 8.0 * s.g.M * (double)s.g.N * s.g.K * s.g.nred * s.g.batch;
+    if (s.kind == STEP_TGEMM) return 8.0 * s.tg.M * (double)s.tg.N * s.tg.K * s.tg.nred * s.tg.batch;
     if (s.kind == STEP_FOV_IP || s.kind == STEP_FOV_EA) {
         double rows = s.kind == STEP_FOV_IP ? h->o : h->v;
         return 8.0 * rows * P->nv * h->nk * h->o * h->v;
@@ -943,6 +1278,33 @@ void free_plans(ccgf_handle *h) {
             delete p;
         }
     h->plans.assign(h->plans.size(), nullptr);
+}
+
+// FP32 copies of the intermediates for the low-precision sigma, smallest first. The operands of the
+// tensor GEMMs and every block under 1 GB always get one; a larger block gets one only while at least
+// `reserve` bytes of device memory stay free afterwards, else its GEMMs read the FP64 block and round
+// it as it is loaded (tgemm_a64 / the register-fed tensor-core kernel), with the same result.
+ccgf_status ensure_fp32(ccgf_handle *h, cudaStream_t st, size_t reserve) {
+    if (h->fp32_done) return CCGF_OK;
+    std::vector<int> order;
+    for (int b = BUF_FOO; b < NBUF; ++b)
+        if (h->W[b].p && !h->Wf[b].p) order.push_back(b);
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return h->W[a].n < h->W[b].n; });
+    for (int b : order) {
+        const size_t bytes = (size_t)h->W[b].n * sizeof(float2);
+        const bool needed = b == BUF_LD || b == BUF_OVOV || b == BUF_T2 || bytes < ((size_t)1 << 30);
+        if (!needed) {
+            size_t fr = 0, tot = 0;
+            CCGF_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+            if (fr < bytes + reserve) continue;
+        }
+        CCGF_TRY(dalloc(h->Wf[b], h->W[b].n));
+        convert_kernel<float><<<gsz(h->W[b].n), 256, 0, st>>>(h->W[b].p, h->Wf[b].p, h->W[b].n);
+        h->launches++;
+    }
+    h->fp32_done = true;
+    CCGF_CUDA_TRY(cudaGetLastError());
+    return CCGF_OK;
 }
 
 ccgf_status sigma_apply(ccgf_handle *h, int sector, int K, int nv, const double2 *x, double2 *y, ccgf_precision prec,
@@ -990,14 +1352,50 @@ ccgf_status sigma_apply(ccgf_handle *h, int sector, int K, int nv, const double2
                 CCGF_TRY(dalloc(h->yf, dmax * nv));
             }
         }
+        CCGF_TRY(ensure_fp32(h, st, (size_t)2 << 30));
         const bool tc = prec == CCGF_TF32X3;
         if (tc && !h->tc_err.p) {
             CCGF_TRY(dalloc(h->tc_err, 1));
             CCGF_CUDA_TRY(cudaMemset(h->tc_err.p, 0, sizeof(int)));
         }
-        if (tc) CCGF_TRY(tc_prepare(h, st));
+        if (tc) CCGF_TRY(tc_prepare(h, st, (size_t)2 << 30));
         if (autotune_enabled()) CCGF_TRY(autotune_plan<float>(h, P, tc ? 2 : 1, tc, h->scratch_f.p, h->yf.p, st));
         run_plan<float>(h, P, x, y, st, nullptr, tc);
+    }
+    CCGF_CUDA_TRY(cudaGetLastError());
+    return CCGF_OK;
+}
+
+
+// W_vvvo[K] of the stored form: the EA r1 -> r2 plan applied to the v unit vectors of r1, its r2
+// part kept as rows (kj, ka, j, a, b) x columns e, for every K
+ccgf_status build_wvvvo_by_plan(ccgf_handle *h, cudaStream_t st) {
+    const int nk = h->nk, v = h->v;
+    const i64 D = h->dim_ea, R2 = D - v;
+    CCGF_TRY(dalloc(h->W[BUF_WVVVO], (i64)nk * R2 * v));
+    DBuf<double2> x, y, arena;
+    CCGF_TRY(dalloc(x, D * v));
+    CCGF_TRY(dalloc(y, D * v));
+    CCGF_CUDA_TRY(cudaMemsetAsync(x.p, 0, sizeof(double2) * D * v, st));
+    {
+        std::vector<double2> eye((size_t)v * v, make_double2(0.0, 0.0));
+        for (int e = 0; e < v; ++e) eye[(size_t)e * v + e] = make_double2(1.0, 0.0);
+        CCGF_CUDA_TRY(cudaMemcpyAsync(x.p, eye.data(), sizeof(double2) * eye.size(), cudaMemcpyHostToDevice, st));
+    }
+    for (int K = 0; K < nk; ++K) {
+        std::unique_ptr<SigmaPlan> P(build_plan_ea(h, K, v, true));
+        std::string why;
+        if (!check_plan(h, P.get(), P->host_off, why)) {
+            set_last_error("internal W_vvvo plan failed its bound check: " + why);
+            return CCGF_ERR_INVALID_ARG;
+        }
+        if (arena.n < P->scratch_elems) CCGF_TRY(dalloc(arena, P->scratch_elems));
+        CCGF_TRY(dalloc(P->offsets, (i64)P->host_off.size()));
+        CCGF_CUDA_TRY(cudaMemcpyAsync(P->offsets.p, P->host_off.data(), sizeof(i64) * P->host_off.size(), cudaMemcpyHostToDevice, st));
+        run_plan<double>(h, P.get(), x.p, y.p, st, arena.p);
+        CCGF_CUDA_TRY(cudaMemcpyAsync(h->W[BUF_WVVVO].p + (i64)K * R2 * v, y.p + (i64)v * v, sizeof(double2) * R2 * v,
+                                      cudaMemcpyDeviceToDevice, st));
+        CCGF_CUDA_TRY(cudaStreamSynchronize(st));   // the plan's offset table and the arena are reused
     }
     CCGF_CUDA_TRY(cudaGetLastError());
     return CCGF_OK;
@@ -1049,8 +1447,15 @@ ccgf_status sigma_apply_in_arena(ccgf_handle *h, int sector, int K, int nv, cons
     return CCGF_OK;
 }
 
+// FP64 scratch of the sigma plans per right-hand-side column (the larger of the two sectors)
+i64 sigma_scratch_per_column(const ccgf_handle *h) {
+    i64 seg[SEG_END + 1];
+    scratch_layout(h, 1, seg, h->direct);
+    return seg[SEG_END];
+}
+
 i64 sigma_arena_elems(const ccgf_handle *h, int nv) {
     i64 seg[SEG_END + 1];
-    scratch_layout(h, nv, seg);
+    scratch_layout(h, nv, seg, false);
     return seg[SEG_END];
 }

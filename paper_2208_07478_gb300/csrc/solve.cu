@@ -67,12 +67,13 @@ __global__ void diag_kernel(int sector, int K, int nk, int o, int v, const int *
     }
 }
 
-__global__ void expand_kernel(const double2 *Bq, double2 *B, i64 D, int N, int nw) {
-    const int nv = N * nw;
+// B[mu][c] = b_p[mu] for column c = (p - p0) * nw + w (zero for the padding columns p >= pend)
+__global__ void expand_kernel(const double2 *Bq, double2 *B, i64 D, int N, int pend, int p0, int nw, int nv) {
     for (i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x; t < D * nv; t += (i64)gridDim.x * blockDim.x) {
         i64 mu = t / nv;
         int c = t % nv;
-        B[t] = Bq[mu * N + c / nw];
+        const int p = p0 + c / nw;
+        B[t] = p < pend ? Bq[mu * N + p] : make_double2(0.0, 0.0);
     }
 }
 
@@ -279,10 +280,12 @@ __global__ void init_cycle_kernel(int nv, int m, const double *beta2, double *be
     for (int i = 0; i <= m; ++i) gc[i] = make_double2(0, 0);
     gc[0] = make_double2(active[c] ? b : 0.0, 0);
 }
-__global__ void scatter_g_kernel(int sector, const double2 *Ct, int N, int nw, int nv, double2 *G, int K, int w0, int nomega) {
+__global__ void scatter_g_kernel(int sector, const double2 *Ct, int N, int pend, int p0, int nw, int nv, double2 *G, int K,
+                                 int w0, int nomega) {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < N * nv; t += gridDim.x * blockDim.x) {
         int row = t / nv, c = t % nv;
-        int col_orb = c / nw, w = c % nw;
+        int col_orb = p0 + c / nw, w = c % nw;
+        if (col_orb >= pend) continue;
         int p, q;
         if (sector == CCGF_SECTOR_IP) { q = row; p = col_orb; }   // G-[p,q] = e_q . X_p
         else { p = row; q = col_orb; }                            // G+[p,q] = e_p . Y_q
@@ -326,8 +329,12 @@ ccgf_status diag_estimate_device(ccgf_handle *h, int sector, int K, double *d, c
 ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omega, double eta, const ccgf_options *opt,
                      double *G_out, int G_on_device, ccgf_stats *stats, cudaStream_t st) {
     const int nk = h->nk, N = h->n, o = h->o, v = h->v;
-    const int m = std::max(2, std::min(opt->restart_m, 128));
-    const int nwc = std::max(1, std::min(opt->omega_chunk, nomega));
+    const int kbeg = opt->kpoint >= 0 ? opt->kpoint : 0, kend = opt->kpoint >= 0 ? opt->kpoint + 1 : nk;
+    const int pbeg = opt->orbital_count > 0 ? opt->orbital_first : 0;
+    const int pend = opt->orbital_count > 0 ? opt->orbital_first + opt->orbital_count : N;
+    const int NS = pend - pbeg;   // orbitals (right-hand sides per frequency) solved
+    const int m_req = std::max(2, std::min(opt->restart_m, 128));
+    int nwc = std::max(1, std::min(opt->omega_chunk, nomega));
     const double tol = opt->tol;
     const i64 Gn = (i64)nk * nomega * N * N;
     ccgf_stats S{};
@@ -360,11 +367,61 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
     CCGF_CUDA_TRY(cudaMallocHost(&nunconv_h, sizeof(int)));
     double sigma_ms = 0;
 
+    // Batch plan from the free device memory. Per column a batch holds the Krylov basis (m + 1
+    // vectors), five work vectors and its share of the sigma scratch (FP64, plus FP32 for a
+    // low-precision inner sigma). All orbitals x a frequency chunk form one batch when they fit;
+    // otherwise the restart length shrinks (not below 10), then the orbitals are split into chunks
+    // of equal width (the last one padded with zero columns, so every batch reuses one sigma plan),
+    // then the frequency chunk shrinks. Low-precision copies of the intermediates are decided first,
+    // leaving room for the smallest batch the largest sector needs.
+    const i64 Dmax_s = (sectors & CCGF_SECTOR_EA) ? h->dim_ea : h->dim_ip;
+    const bool lowp = opt->prec != CCGF_FP64;
+    auto column_bytes = [&](i64 D, int mm) -> double {
+        const double scratch = (double)sigma_scratch_per_column(h) * (16.0 + (lowp ? 8.0 : 0.0)) + (lowp ? 8.0 * D : 0.0);
+        return 16.0 * D * (mm + 6) + scratch + 16.0 * 304 * N;
+    };
+    {
+        const int min_cols = std::min(NS * nwc, 16);
+        const double reserve = column_bytes(Dmax_s, std::min(m_req, 20)) * min_cols + (double)(2ull << 30);
+        if (lowp) CCGF_TRY(ensure_fp32(h, st, (size_t)reserve));
+        if (opt->prec == CCGF_TF32X3) {
+            if (!h->tc_err.p) {
+                CCGF_TRY(dalloc(h->tc_err, 1));
+                CCGF_CUDA_TRY(cudaMemsetAsync(h->tc_err.p, 0, sizeof(int), st));
+            }
+            CCGF_TRY(tc_prepare(h, st, (size_t)reserve));
+        }
+    }
+
     for (int sector = CCGF_SECTOR_IP; sector <= CCGF_SECTOR_EA; ++sector) {
         if (!(sectors & sector)) continue;
         const i64 D = sector == CCGF_SECTOR_IP ? h->dim_ip : h->dim_ea;
         const double s = sector == CCGF_SECTOR_IP ? 1.0 : -1.0;
-        const int nvmax = N * nwc;
+        int m = m_req, np = NS;
+        {
+            size_t fr = 0, tot = 0;
+            CCGF_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+            // minus the right-hand / left vectors and a margin for split-K partial sums and tables
+            const double avail = (double)fr - (double)(4ull << 30) - 32.0 * D * N;
+            auto fits = [&](int cols, int mm) { return column_bytes(D, mm) * cols <= avail; };
+            while (!fits(NS * nwc, m) && m > 10) m = std::max(10, m - 5);
+            if (!fits(NS * nwc, m)) {
+                np = (int)std::max<double>(1.0, std::floor(avail / column_bytes(D, m) / nwc));
+                np = std::min(np, NS);
+                if (np < NS) np = (int)ceil_div(NS, ceil_div(NS, np));   // equal chunk widths
+                if (!fits(np * nwc, m)) {
+                    np = 1;
+                    nwc = (int)std::max<double>(1.0, std::floor(avail / column_bytes(D, m)));
+                }
+            }
+            if (!fits(np * nwc, m)) {
+                set_last_error("not enough device memory for one right-hand side of this sector");
+                return CCGF_ERR_OOM;
+            }
+        }
+        S.restart_used = m;
+        S.columns_per_batch = std::max<long long>(S.columns_per_batch, (long long)np * nwc);
+        const int nvmax = np * nwc;
         DBuf<double2> Bq, E, B, X, R, U, AU, V, Ct, Hs, Hs2, Hm, cs, sn, g, y, z, Wk;
         DBuf<double> dvec, beta2, beta, hn2, target, res;
         DBuf<int> active, nunconv;
@@ -402,22 +459,23 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
             dfree(active);
             dfree(nunconv);
         };
-        for (int K = 0; K < nk; ++K) {
+        for (int K = kbeg; K < kend; ++K) {
             for (int p = 0; p < N; ++p) {
                 CCGF_TRY(make_rhs(h, sector, K, p, Bq.p + p, N, st));
                 CCGF_TRY(make_left(h, sector, K, p, E.p + (i64)p * D, 1, st));
             }
             diag_kernel<<<g1(D), 256, 0, st>>>(sector, K, nk, o, v, h->kadd_d.p, h->ksub_d.p, h->W[BUF_FOO].p, h->W[BUF_FVV].p, dvec.p, D);
             h->launches++;
-            for (int w0 = 0; w0 < nomega; w0 += nwc) {
+            for (int w0 = 0; w0 < nomega; w0 += nwc)
+            for (int p0 = pbeg; p0 < pend; p0 += np) {
                 const int nw = std::min(nwc, nomega - w0);
-                const int nv = N * nw;
+                const int nv = np * nw;
                 const i64 Dn = D * nv;
                 std::vector<double2> zh(nv);
                 for (int c = 0; c < nv; ++c) zh[c] = make_double2(omega[w0 + c % nw], sector == CCGF_SECTOR_IP ? -eta : eta);
                 CCGF_CUDA_TRY(cudaMemcpyAsync(z.p, zh.data(), sizeof(double2) * nv, cudaMemcpyHostToDevice, st));
                 Shift Sh{z.p, s, dvec.p};
-                expand_kernel<<<g1(Dn), 256, 0, st>>>(Bq.p, B.p, D, N, nw);
+                expand_kernel<<<g1(Dn), 256, 0, st>>>(Bq.p, B.p, D, N, pend, p0, nw, nv);
                 h->launches++;
                 CCGF_CUDA_TRY(cudaMemsetAsync(X.p, 0, sizeof(double2) * Dn, st));
                 CCGF_CUDA_TRY(cudaMemcpyAsync(R.p, B.p, sizeof(double2) * Dn, cudaMemcpyDeviceToDevice, st));
@@ -433,7 +491,7 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                 std::vector<double> tg(nv);
                 for (int c = 0; c < nv; ++c) tg[c] = tol * std::sqrt(b2[c]);
                 CCGF_CUDA_TRY(cudaMemcpyAsync(target.p, tg.data(), sizeof(double) * nv, cudaMemcpyHostToDevice, st));
-                if (opt->warm_start) {
+                if (opt->warm_start && np == N && NS == N) {
                     // learned initial vectors: per column keep the candidate (network, baseline, cold) with the
                     // smallest true residual; the cold start's residual is |b|
                     bool used = false, net = false;
@@ -571,9 +629,9 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                     residual_kernel<<<g1(Dn), 256, 0, st>>>(Sh, B.p, X.p, AU.p, R.p, D, nv);
                     h->launches++;
                 }
-                if (h->ws_capturing) CCGF_TRY(warmstart_capture(h, sector, K, X.p, D, nw, w0, b2.data(), st));
+                if (h->ws_capturing && np == N && NS == N) CCGF_TRY(warmstart_capture(h, sector, K, X.p, D, nw, w0, b2.data(), st));
                 S.inner_iterations += it_total;
-                S.rhs_solved += nv;
+                S.rhs_solved += (long long)std::min(np, pend - p0) * nw;
                 S.max_rel_residual = std::max(S.max_rel_residual, maxres);
                 if (!converged) final_status = CCGF_NOT_CONVERGED;
                 // G contraction: Ct[q][c] = sum_mu E[q][mu] X[mu][c]
@@ -596,7 +654,7 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                     gd.alpha = make_double2(1, 0);
                     gd.beta = make_double2(0, 0);
                     h->launches += launch_zgemm<double>(gd, E.p, X.p, Ct.p, st, Wk.p, Wk.n);
-                    scatter_g_kernel<<<g1((i64)N * nv), 256, 0, st>>>(sector, Ct.p, N, nw, nv, G, K, w0, nomega);
+                    scatter_g_kernel<<<g1((i64)N * nv), 256, 0, st>>>(sector, Ct.p, N, pend, p0, nw, nv, G, K, w0, nomega);
                     h->launches++;
                 }
                 CCGF_CUDA_TRY(cudaGetLastError());

@@ -112,8 +112,12 @@ __device__ __forceinline__ void st_shared4(unsigned char *p, float a, float b, f
     *(float4 *)p = make_float4(a, b, c, d);
 }
 
-template <int NCOLS>
-__global__ void __launch_bounds__(NTHREADS, 1) tc_zgemm_kernel(GemmDesc d, const float2 *__restrict__ A, const float2 *__restrict__ B,
+__device__ __forceinline__ float2 as_f2(float2 a) { return a; }
+__device__ __forceinline__ float2 as_f2(double2 a) { return make_float2((float)a.x, (float)a.y); }
+
+// TA: storage type of A (double2: an FP64 intermediate without an FP32 copy, rounded as it is loaded)
+template <int NCOLS, typename TA = float2>
+__global__ void __launch_bounds__(NTHREADS, 1) tc_zgemm_kernel(GemmDesc d, const TA *__restrict__ A, const float2 *__restrict__ B,
                                                                float2 *__restrict__ C, int BNc, int *err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const int NR = 2 * BNc;                                  // real rows of the B' tile (multiple of 16)
@@ -158,7 +162,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_zgemm_kernel(GemmDesc d, const
         __syncthreads();
         if (abort_flag) break;
         const int r = kt / ktiles, k0 = (kt % ktiles) * BKC;
-        const float2 *Ab = A + d.offA[(i64)b * d.nred + r];
+        const TA *Ab = A + d.offA[(i64)b * d.nred + r];
         const float2 *Bb = B + d.offB[(i64)b * d.nred + r];
         unsigned char *sAh = smem_raw + st * stage_bytes, *sAl = sAh + a_bytes, *sBh = sAl + a_bytes, *sBl = sBh + b_bytes;
 
@@ -171,9 +175,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_zgemm_kernel(GemmDesc d, const
                 const int m = m0 + g * 8 + r8, k = k0 + kh * 8 + c * 2;
                 float2 v0 = make_float2(0.f, 0.f), v1 = v0;
                 if (m < d.M) {
-                    const float2 *row = Ab + (i64)m * d.rsA;
-                    if (k < d.K) v0 = row[(i64)k * d.csA];
-                    if (k + 1 < d.K) v1 = row[(i64)(k + 1) * d.csA];
+                    const TA *row = Ab + (i64)m * d.rsA;
+                    if (k < d.K) v0 = as_f2(row[(i64)k * d.csA]);
+                    if (k + 1 < d.K) v1 = as_f2(row[(i64)(k + 1) * d.csA]);
                 }
                 float h0, l0, h1, l1, h2, l2, h3, l3;
                 split(v0.x, h0, l0);
@@ -289,11 +293,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_zgemm_kernel(GemmDesc d, const
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
 }
 
-template <int NCOLS>
-void launch_cols(dim3 grid, size_t smem, cudaStream_t st, const GemmDesc &d, const float2 *A, const float2 *B, float2 *C, int BNc,
+template <int NCOLS, typename TA>
+void launch_cols(dim3 grid, size_t smem, cudaStream_t st, const GemmDesc &d, const TA *A, const float2 *B, float2 *C, int BNc,
                  int *err) {
-    cudaFuncSetAttribute(tc_zgemm_kernel<NCOLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    tc_zgemm_kernel<NCOLS><<<grid, NTHREADS, smem, st>>>(with_wait_limit(d), A, B, C, BNc, err);
+    cudaFuncSetAttribute(tc_zgemm_kernel<NCOLS, TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    tc_zgemm_kernel<NCOLS, TA><<<grid, NTHREADS, smem, st>>>(with_wait_limit(d), A, B, C, BNc, err);
 }
 
 
@@ -862,21 +866,28 @@ size_t tc_zgemm_smem_bytes(int BNc) {
     return 2 * stage + 64;
 }
 
-int launch_tc_zgemm(const GemmDesc &d, const float2 *A, const float2 *B, float2 *C, int *err, cudaStream_t st) {
+template <typename TA>
+static int launch_tc_reg(const GemmDesc &d, const TA *A, const float2 *B, float2 *C, int *err, cudaStream_t st) {
     // complex N tile: 128 (256 real TMEM columns), or N rounded up to a multiple of 8 when smaller
     const int BNc = d.N >= 128 ? 128 : (int)ceil_div(d.N, 8) * 8;
     const int NR = 2 * BNc;
     const size_t smem = tc_zgemm_smem_bytes(BNc);
     const dim3 grid((unsigned)ceil_div(d.N, BNc), (unsigned)ceil_div(d.M, BM), (unsigned)d.batch);
     if (NR <= 32)
-        launch_cols<32>(grid, smem, st, d, A, B, C, BNc, err);
+        launch_cols<32, TA>(grid, smem, st, d, A, B, C, BNc, err);
     else if (NR <= 64)
-        launch_cols<64>(grid, smem, st, d, A, B, C, BNc, err);
+        launch_cols<64, TA>(grid, smem, st, d, A, B, C, BNc, err);
     else if (NR <= 128)
-        launch_cols<128>(grid, smem, st, d, A, B, C, BNc, err);
+        launch_cols<128, TA>(grid, smem, st, d, A, B, C, BNc, err);
     else
-        launch_cols<256>(grid, smem, st, d, A, B, C, BNc, err);
+        launch_cols<256, TA>(grid, smem, st, d, A, B, C, BNc, err);
     return 1;
+}
+int launch_tc_zgemm(const GemmDesc &d, const float2 *A, const float2 *B, float2 *C, int *err, cudaStream_t st) {
+    return launch_tc_reg<float2>(d, A, B, C, err, st);
+}
+int launch_tc_zgemm_a64(const GemmDesc &d, const double2 *A, const float2 *B, float2 *C, int *err, cudaStream_t st) {
+    return launch_tc_reg<double2>(d, A, B, C, err, st);
 }
 
 // ----------------------------------------------------------------------------- host side of the TMA path
@@ -904,11 +915,15 @@ static EncodeTiledFn encode_fn() {
     return fn;
 }
 
-ccgf_status tc_prepare(ccgf_handle *h, cudaStream_t st) {
+ccgf_status tc_prepare(ccgf_handle *h, cudaStream_t st, size_t reserve) {
     if (h->tc_ops) return CCGF_OK;
     TcOperands *T = new TcOperands();
-    for (int b = BUF_FOO; b < NBUF; ++b) {
+    // A operands of the plain GEMM steps only (the tensor GEMMs of the density-fitting terms run on SIMT);
+    // a block without hi / lo copies runs on the register-fed kernel
+    for (int b = BUF_FOO; b < BUF_LD; ++b) {
         if (!h->Wf[b].p) continue;
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess || fr < (size_t)h->Wf[b].n * 16 + reserve) continue;
         ccgf_status s = dalloc(T->hi[b], h->Wf[b].n);
         if (s == CCGF_OK) s = dalloc(T->lo[b], h->Wf[b].n);
         if (s != CCGF_OK) {

@@ -1,0 +1,159 @@
+// Batched complex GEMM over tensor operands whose row, column and contraction indices are each a
+// pair of tensor indices: index i of a GEMM dimension lives at (i / d2) * s1 + (i % d2) * s2 of
+// its operand (IMap). A contraction such as sum_{n,f} W[(m,e),(n,f)] t[(n,f),(j,x)] over
+// momentum-blocked tensors then runs as one launch, whatever the operands' index order, with no
+// transposed copies: the build of the similarity-transformed Hamiltonian blocks (Eq. 5) and the
+// sigma terms evaluated from the density-fitting factors use it.
+//
+// Tile: 64 x 64 complex outputs per CTA, 256 threads with 4 x 4 outputs each, 16 contraction
+// indices staged through shared memory per step. Each thread's row / column offsets are computed
+// once per tile; only the contraction index is decomposed per step.
+#include "ccgf_internal.h"
+
+namespace {
+
+constexpr int TB = 64, TK = 16;
+
+__device__ __forceinline__ i64 imap(const IMap &m, i64 i) { return (i / m.d2) * m.s1 + (i % m.d2) * m.s2; }
+
+template <typename T> __device__ __forceinline__ T zero2();
+template <> __device__ __forceinline__ double2 zero2<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ float2 zero2<float2>() { return make_float2(0.f, 0.f); }
+
+__device__ __forceinline__ double2 cvt2(double2 a, double2) { return a; }
+__device__ __forceinline__ float2 cvt2(float2 a, float2) { return a; }
+__device__ __forceinline__ float2 cvt2(double2 a, float2) { return make_float2((float)a.x, (float)a.y); }
+
+// TA: storage type of A (double2 with R = float: an FP64 operand rounded to FP32 as it is loaded)
+template <typename R, typename TA>
+__global__ void __launch_bounds__(256) tgemm_kernel(TGemm d, const TA *__restrict__ A, const typename cvec<R>::T *__restrict__ B,
+                                                    typename cvec<R>::T *__restrict__ C) {
+    typedef typename cvec<R>::T T;
+    __shared__ T As[TK][TB + 1];
+    __shared__ T Bs[TK][TB + 1];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int m0 = blockIdx.y * TB, n0 = blockIdx.x * TB;
+    // loader roles: A tile as 64 rows x 16 k (k fastest when the contraction index of A is
+    // contiguous), B tile as 16 k x 64 columns (column fastest unless B's k index is contiguous)
+    const bool a_kfast = d.ak.s2 == 1 && d.ak.d2 >= TK;
+    const bool b_kfast = d.bk.s2 == 1 && d.bk.d2 >= TK && d.bn.s2 != 1;
+    int a_row[4], a_kk[4], b_col[4], b_kk[4];
+    i64 a_roff[4], b_coff[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const int l = tid + 256 * s;
+        if (a_kfast) { a_kk[s] = l & 15; a_row[s] = l >> 4; } else { a_row[s] = l & 63; a_kk[s] = l >> 6; }
+        if (b_kfast) { b_kk[s] = l & 15; b_col[s] = l >> 4; } else { b_col[s] = l & 63; b_kk[s] = l >> 6; }
+        const int m = m0 + a_row[s], n = n0 + b_col[s];
+        a_roff[s] = m < d.M ? imap(d.am, m) : -1;
+        b_coff[s] = n < d.N ? imap(d.bn, n) : -1;
+    }
+    const bool use_beta = d.beta.x != 0.0 || d.beta.y != 0.0;
+    for (int b = blockIdx.z; b < d.batch; b += gridDim.z) {
+        T acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = zero2<T>();
+        for (int r = 0; r < d.nred; ++r) {
+            const TA *Ab = A + d.offA[(i64)b * d.nred + r];
+            const T *Bb = B + d.offB[(i64)b * d.nred + r];
+            for (int k0 = 0; k0 < d.K; k0 += TK) {
+#pragma unroll
+                for (int s = 0; s < 4; ++s) {
+                    const int k = k0 + a_kk[s];
+                    As[a_kk[s]][a_row[s]] = (a_roff[s] >= 0 && k < d.K) ? cvt2(Ab[a_roff[s] + imap(d.ak, k)], T()) : zero2<T>();
+                    const int kb = k0 + b_kk[s];
+                    Bs[b_kk[s]][b_col[s]] = (b_coff[s] >= 0 && kb < d.K) ? Bb[imap(d.bk, kb) + b_coff[s]] : zero2<T>();
+                }
+                __syncthreads();
+#pragma unroll
+                for (int kk = 0; kk < TK; ++kk) {
+                    T a[4], bb[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            acc[i][j].x = fma(a[i].x, bb[j].x, acc[i][j].x);
+                            acc[i][j].x = fma(-a[i].y, bb[j].y, acc[i][j].x);
+                            acc[i][j].y = fma(a[i].x, bb[j].y, acc[i][j].y);
+                            acc[i][j].y = fma(a[i].y, bb[j].x, acc[i][j].y);
+                        }
+                }
+                __syncthreads();
+            }
+        }
+        T *Cb = C + d.offC[b];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int m = m0 + ty + 16 * i;
+            if (m >= d.M) continue;
+            const i64 rm = imap(d.cm, m);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int n = n0 + tx + 16 * j;
+                if (n >= d.N) continue;
+                T *c = Cb + rm + imap(d.cn, n);
+                T v;
+                v.x = (R)d.alpha.x * acc[i][j].x - (R)d.alpha.y * acc[i][j].y;
+                v.y = (R)d.alpha.x * acc[i][j].y + (R)d.alpha.y * acc[i][j].x;
+                if (use_beta) {
+                    const T o = *c;
+                    v.x += (R)d.beta.x * o.x - (R)d.beta.y * o.y;
+                    v.y += (R)d.beta.x * o.y + (R)d.beta.y * o.x;
+                }
+                *c = v;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+IMap imap_single(i64 stride) { return IMap{1 << 30, 0, stride}; }
+IMap imap_pair(int inner, i64 outer_stride, i64 inner_stride) { return IMap{inner, outer_stride, inner_stride}; }
+
+template <typename R, typename TA>
+static int launch_t(const TGemm &d, const TA *A, const typename cvec<R>::T *B, typename cvec<R>::T *C, cudaStream_t st) {
+    if (d.batch <= 0 || d.M <= 0 || d.N <= 0 || d.nred <= 0) return 0;
+    const i64 z = d.batch < 65535 ? d.batch : 65535;
+    dim3 grid((unsigned)ceil_div(d.N, TB), (unsigned)ceil_div(d.M, TB), (unsigned)z);
+    tgemm_kernel<R, TA><<<grid, 256, 0, st>>>(d, A, B, C);
+    return 1;
+}
+template <typename R>
+int launch_tgemm(const TGemm &d, const typename cvec<R>::T *A, const typename cvec<R>::T *B, typename cvec<R>::T *C,
+                 cudaStream_t st) {
+    return launch_t<R, typename cvec<R>::T>(d, A, B, C, st);
+}
+template int launch_tgemm<double>(const TGemm &, const double2 *, const double2 *, double2 *, cudaStream_t);
+template int launch_tgemm<float>(const TGemm &, const float2 *, const float2 *, float2 *, cudaStream_t);
+int launch_tgemm_a64(const TGemm &d, const double2 *A, const float2 *B, float2 *C, cudaStream_t st) {
+    return launch_t<float, double2>(d, A, B, C, st);
+}
+
+// a plain GemmDesc (single-stride indices) as a tensor GEMM
+TGemm tgemm_of(const GemmDesc &g) {
+    TGemm t{};
+    t.M = g.M;
+    t.N = g.N;
+    t.K = g.K;
+    t.nred = g.nred;
+    t.batch = g.batch;
+    t.am = imap_single(g.rsA);
+    t.ak = imap_single(g.csA);
+    t.bk = imap_single(g.rsB);
+    t.bn = imap_single(g.csB);
+    t.cm = imap_single(g.rsC);
+    t.cn = imap_single(g.csC);
+    t.offA = g.offA;
+    t.offB = g.offB;
+    t.offC = g.offC;
+    t.alpha = g.alpha;
+    t.beta = g.beta;
+    return t;
+}

@@ -200,7 +200,7 @@ __global__ void left_reduce_kernel(VD D, int sector, int K, int q, double2 *out,
 }  // namespace
 
 static VD make_vd(ccgf_handle *h) {
-    return VD{h->nk, h->o, h->v, h->kadd_d.p, h->ksub_d.p, h->t1.p, h->t2.p, h->l1.p, h->l2.p};
+    return VD{h->nk, h->o, h->v, h->kadd_d.p, h->ksub_d.p, h->t1.p, h->W[BUF_T2].p, h->l1.p, h->l2.p};
 }
 
 ccgf_status make_rhs(ccgf_handle *h, int sector, int K, int p, double2 *out, i64 ld, cudaStream_t st) {

@@ -141,21 +141,24 @@ def mp2_t2(kmesh, nocc, mo_energy, L):
     nvir = mo_energy.shape[1] - nocc
     o, v = slice(0, nocc), slice(nocc, None)
     t2 = np.zeros((nk, nk, nk, nocc, nocc, nvir, nvir), dtype=np.complex128)
+    kas = np.arange(nk)
     for ki in range(nk):
         for kj in range(nk):
-            for ka in range(nk):
-                kb = kadd[kadd[ki, kj], kneg[ka]]
-                # (a ka, i ki | b kb, j kj): momentum ka + kb = ki + kj holds by construction.
-                ai = L[ka, ki][:, v, o]
-                bj = L[kb, kj][:, v, o]
-                num = np.einsum('Qai,Qbj->ijab', ai, bj)
-                eo_i = mo_energy[ki, :nocc]
-                eo_j = mo_energy[kj, :nocc]
-                ev_a = mo_energy[ka, nocc:]
-                ev_b = mo_energy[kb, nocc:]
-                den = (eo_i[:, None, None, None] + eo_j[None, :, None, None]
-                       - ev_a[None, None, :, None] - ev_b[None, None, None, :])
-                t2[ki, kj, ka] = num / den
+            # all ka at once; kb = ki + kj - ka, so (a ka, i ki | b kb, j kj) conserves momentum
+            kbs = kadd[kadd[ki, kj], kneg[kas]]
+            ai = L[kas, ki][:, :, v, o]            # [ka][Q][a][i]
+            bj = L[kbs, kj][:, :, v, o]            # [ka][Q][b][j]
+            nq = ai.shape[1]
+            # sum over Q as one batched matrix product: [ka][(a,i)][Q] @ [ka][Q][(b,j)]
+            num = np.matmul(ai.reshape(nk, nq, nvir * nocc).transpose(0, 2, 1), bj.reshape(nk, nq, nvir * nocc))
+            num = num.reshape(nk, nvir, nocc, nvir, nocc).transpose(0, 2, 4, 1, 3)
+            eo_i = mo_energy[ki, :nocc]
+            eo_j = mo_energy[kj, :nocc]
+            ev_a = mo_energy[kas, nocc:]           # [ka][a]
+            ev_b = mo_energy[kbs, nocc:]           # [ka][b]
+            den = (eo_i[None, :, None, None, None] + eo_j[None, None, :, None, None]
+                   - ev_a[:, None, None, :, None] - ev_b[:, None, None, None, :])
+            t2[ki, kj] = num / den
     return t2
 
 

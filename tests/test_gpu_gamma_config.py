@@ -1,9 +1,12 @@
 """The Gamma-point IP workload (1x1x1 mesh, nocc 4, nvir 12, Naux 48, 16 frequencies in
 [-1, 1] Ha, eta 0.01; T1 = 0, T2 the MP2 amplitudes), the nk = 1 limit of Eq. 9: all 16
 orbitals at all 16 frequencies on the GPU against the oracle's dense LU solves of the
-explicit EOM-IP matrix (dimension 196).
-  plain FP64 at tol 1e-12: |dG| <= 1e-8 per element;
-  chosen forms at tol 1e-6: |dG| <= 1e-6 max(1, |G|) per element.
+explicit EOM-IP matrix (dimension 196). Here the frequency window holds poles of G.
+  plain FP64 at tol 1e-12:               |dG| <= 1e-8 per element;
+  chosen forms at tol 1e-10:             |dG| <= 1e-6 max(1, |G|) per element (precision);
+  every form at the benchmark's tol 1e-6: |dG_pq| <= |e_q| |M(w)^-1|_2 tol |b_p|, the bound a
+      relative residual tol implies (M = w - i eta + A_IP, its inverse norm from the dense
+      matrix); the per-element distribution of |dG| / max(1, |G|) is printed.
 """
 import numpy as np
 import pytest
@@ -29,22 +32,42 @@ def case():
     Bm = np.stack([ke.rhs_ip(0, p) for p in range(n)], 1)
     Em = np.stack([ke.left_ip(0, q) for q in range(n)], 0)
     Gref = solvers.dense_gf("ip", A, Bm, Em, s.omega, s.eta)
+    inv_norm = np.array([1.0 / np.linalg.svd(solvers.shift_matrix("ip", om, s.eta, A), compute_uv=False)[-1]
+                         for om in s.omega])
+    bound = (inv_norm[:, None, None] * np.linalg.norm(Bm, axis=0)[None, :, None]
+             * np.linalg.norm(Em, axis=1)[None, None, :])           # [w, p, q] per unit tolerance
     h = B.build_intermediates(s.kmesh, s.nocc, s.nvir, s.naux, s.mo_energy, s.L, s.t1, s.t2)
-    yield s, h, Gref
+    yield s, h, Gref, bound
     h.close()
 
 
-@pytest.mark.parametrize("prec,tol", [(B.FP64, 1e-12), (B.TF32X3, 1e-6), (B.FP32, 1e-6)],
-                         ids=["fp64", "tf32x3", "fp32"])
-def test_gamma_ip_all_orbitals_all_frequencies(case, prec, tol):
-    s, h, Gref = case
+def solve(s, h, prec, tol):
     G = np.zeros((1, len(s.omega), s.nmo, s.nmo), dtype=np.complex128)
     opt = B.default_options(prec=prec, tol=tol, restart_m=40, max_iter=4000, max_refine=40, omega_chunk=4)
     st, stats = B.solve_gf(h, B.IP, s.omega, s.eta, G, options=opt)
     assert st == B.CCGF_OK
     assert stats["rhs_solved"] == s.nmo * len(s.omega)
-    d = np.abs(G[0] - Gref)
+    assert stats["max_rel_residual"] <= tol
+    return G[0]
+
+
+@pytest.mark.parametrize("prec,tol", [(B.FP64, 1e-12), (B.TF32X3, 1e-10), (B.FP32, 1e-10)], ids=["fp64", "tf32x3", "fp32"])
+def test_gamma_ip_all_orbitals_all_frequencies(case, prec, tol):
+    s, h, Gref, bound = case
+    d = np.abs(solve(s, h, prec, tol) - Gref)
     if prec == B.FP64:
         assert d.max() <= 1e-8, d.max()
     else:
         assert (d / np.maximum(1.0, np.abs(Gref))).max() <= 1e-6, d.max()
+
+
+@pytest.mark.parametrize("prec", [B.FP64, B.TF32X3, B.FP32], ids=["fp64", "tf32x3", "fp32"])
+def test_gamma_ip_at_benchmark_tolerance(case, prec):
+    s, h, Gref, bound = case
+    tol = 1e-6
+    d = np.abs(solve(s, h, prec, tol) - Gref)
+    rel = d / np.maximum(1.0, np.abs(Gref))
+    q = np.quantile(rel, [0.5, 0.9, 0.99, 1.0])
+    print(f"prec {prec} tol 1e-6: |dG|/max(1,|G|) quantiles 50/90/99/100 %: {q[0]:.2e} {q[1]:.2e} {q[2]:.2e} {q[3]:.2e};"
+          f" largest |dG| / (residual bound) {(d / (tol * bound)).max():.2e}")
+    assert np.all(d <= tol * bound)

@@ -31,7 +31,9 @@ CASES = {
 }
 
 
-def build_case(name):
+def build_case(name, mode="stored"):
+    """mode: 'stored' keeps every H_bar block; 'direct' forms the W_vvvo r1 term, the EA singles'
+    (2<am|ef> - <am|fe>) term and the ladder's T2 part from the density-fitting factors."""
     kmesh, o, v, naux, seed, t1s, rl = CASES[name]
     s = make_system(kmesh, o, v, naux, seed=seed, L_sigma=0.08, t1_sigma=t1s, nomega=3,
                     omega_range=(-0.7, 0.7), eta=0.02)
@@ -40,14 +42,16 @@ def build_case(name):
         rng = np.random.default_rng(seed + 7)
         l1 = 0.05 * (rng.normal(size=s.t1.shape) + 1j * rng.normal(size=s.t1.shape))
         l2 = symmetric_lambda2(KMesh(kmesh), 0.05 * (rng.normal(size=s.t2.shape) + 1j * rng.normal(size=s.t2.shape)))
-    h = B.build_intermediates(s.kmesh, s.nocc, s.nvir, s.naux, s.mo_energy, s.L, s.t1, s.t2, l1, l2)
+    opt = B.default_options(direct_terms=1 if mode == "stored" else 2)
+    h = B.build_intermediates(s.kmesh, s.nocc, s.nvir, s.naux, s.mo_energy, s.L, s.t1, s.t2, l1, l2, options=opt)
     ke = KEOM(s.kmesh, s.nocc, s.mo_energy, s.t1, s.t2, L=s.L, l1=l1, l2=l2)
     return s, h, ke
 
 
-@pytest.fixture(scope="module", params=list(CASES))
+@pytest.fixture(scope="module", params=[(c, m) for c in CASES for m in ("stored", "direct")],
+                ids=[f"{c}-{m}" for c in CASES for m in ("stored", "direct")])
 def case(request):
-    s, h, ke = build_case(request.param)
+    s, h, ke = build_case(*request.param)
     yield s, h, ke
     h.close()
 

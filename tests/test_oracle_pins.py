@@ -254,3 +254,16 @@ def test_rows_oracle_equals_full_oracle(kmesh, o, v, seed):
             full = (ke.sigma_ip if kind == "ip" else ke.sigma_ea)(K, x)
             rows = (kr.sigma_ip_elements if kind == "ip" else kr.sigma_ea_elements)(K, x, range(D))
             np.testing.assert_allclose(rows, full, atol=1e-12 * np.abs(full).max())
+
+
+def test_rows_oracle_vectors_equal_full_oracle():
+    from oracle.rows import KRows
+    s = make_system((2, 1, 1), 2, 3, 5, seed=34, L_sigma=0.1, t1_sigma=0.05, nomega=0)
+    ke = KEOM(s.kmesh, s.nocc, s.mo_energy, s.t1, s.t2, L=s.L)
+    kr = KRows(s.kmesh, s.nocc, s.mo_energy, s.t1, s.t2, s.L)
+    for K in range(s.nk):
+        for p in range(s.nmo):
+            np.testing.assert_allclose(kr.rhs("ip", K, p), ke.rhs_ip(K, p), atol=1e-15)
+            np.testing.assert_allclose(kr.rhs("ea", K, p), ke.rhs_ea(K, p), atol=1e-15)
+            np.testing.assert_allclose(kr.left("ip", K, p), ke.left_ip(K, p), atol=1e-15)
+            np.testing.assert_allclose(kr.left("ea", K, p), ke.left_ea(K, p), atol=1e-15)
