@@ -129,6 +129,10 @@ typedef struct {
     long long columns_per_batch;/* largest number of right-hand sides solved together: all
                                    orbitals x omega_chunk frequencies when they fit in device
                                    memory, else orbital chunks of equal width             */
+    double vector_ms;           /* device time of the Arnoldi vector steps after each sigma
+                                   (shift, both CGS passes, norm, normalisation)           */
+    double vector_bytes;        /* their algorithmic HBM traffic: 16 (4J + 12) D nv bytes per
+                                   step with J basis vectors (vector_bytes / vector_ms: GB/s) */
 } ccgf_stats;
 
 typedef struct ccgf_handle ccgf_handle;
@@ -179,6 +183,45 @@ ccgf_status ccgf_left(ccgf_handle *h, int sector, int K, int p, double *out, voi
 ccgf_status ccgf_solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omega,
                           double eta, const ccgf_options *opt, double *G_out, int G_on_device,
                           ccgf_stats *stats, void *stream);
+
+/* Model-order-reduction CCGF (the paper's MOR frequency interpolation): G_pq(k,w) of Eq. 9 on the
+ * nomega grid frequencies from a reduced model per (sector, k). The shifted systems are solved (as in
+ * ccgf_solve_gf, with opt) at the n_mor model frequencies omega_mor (1..64, host array) for every
+ * orbital; an orthonormal basis V of the span of those solutions (Gram matrix diagonalised, directions
+ * with singular value below 1e-7 of the largest dropped) projects the EOM operator, the right-hand
+ * sides and the left vectors (A_r = V^H A V, b_r = V^H b, e_r = e V); the reduced systems of dimension
+ * rank(V) <= nmo n_mor are then solved at every grid frequency. G is exact (up to the solver
+ * tolerance) at the model frequencies. opt->kpoint selects one k (-1: all); the orbital slice and the
+ * warm start of opt are ignored. stats: the model solves' counters, columns_per_batch = the largest
+ * reduced dimension. G_out as ccgf_solve_gf. Synchronises. Errors as ccgf_solve_gf. */
+ccgf_status ccgf_solve_gf_mor(ccgf_handle *h, int sectors, int n_mor, const double *omega_mor, int nomega, const double *omega,
+                              double eta, const ccgf_options *opt, double *G_out, int G_on_device, ccgf_stats *stats,
+                              void *stream);
+
+/* Spectral function and density of states (Eq. 10): A(k,w) = -(1/pi) Im G(k,w); its trace over the
+ * orbitals is the k-resolved density of states
+ *   dos[k][w] = -(1/pi) Im sum_p G[k][w][p][p]                        (G_minus == NULL)
+ *   dos[k][w] = -(1/pi) Im sum_p G[k][w][p][p] + (1/pi) Im sum_p G_minus[k][w][p][p]
+ * G: complex [nk][nomega][nmo][nmo] as ccgf_solve_gf writes it (the time-ordered G = G+ + G-, whose
+ * removal part gives negative -Im G / pi below the gap); with G_minus != NULL, G holds the addition
+ * part G+ (a solve with CCGF_SECTOR_EA) and G_minus the removal part G- (CCGF_SECTOR_IP), which enters
+ * with the opposite sign (the retarded convention: positive peaks on both sides of the gap).
+ * dos: real [nk][nomega]; dos_total (NULL allowed): real [nomega], (1/nk) sum_k dos[k]. All device
+ * pointers, caller-owned; stream-ordered, no synchronisation. Errors: INVALID_ARG, CUDA. */
+ccgf_status ccgf_spectral_function(int nk, int nomega, int nmo, const double *G, const double *G_minus, double *dos,
+                                   double *dos_total, void *stream);
+
+/* Active-space self-energy correction (Eqs. 12-14), for every k and frequency:
+ *   Sigma_CAS = G_GW,CAS^-1 - G_CC,CAS^-1,  Sigma_full = V Sigma_CAS V^+,  G_out = [G_GW^-1 - Sigma_full]^-1.
+ * V: complex [nk][nmo][nact], natural-orbital coefficients of the nact active orbitals (Eq. 11);
+ * G_gw: complex [nk][nomega][nmo][nmo] (GW, full space); G_gw_cas, G_cc_cas: complex
+ * [nk][nomega][nact][nact] (GW and coupled cluster in the active space, e.g. ccgf_solve_gf on the
+ * active-space system); G_out: complex [nk][nomega][nmo][nmo]. The GW Green's functions are inputs
+ * (computing them is outside this library). Device pointers, caller-owned; one thread block per (k, w)
+ * inverts in shared memory (nmo <= 110). Synchronises the stream to read the singularity flag.
+ * Errors: INVALID_ARG (sizes, NULL, a singular matrix), CUDA. */
+ccgf_status ccgf_self_energy_correction(int nk, int nomega, int nmo, int nact, const double *V, const double *G_gw,
+                                        const double *G_gw_cas, const double *G_cc_cas, double *G_out, void *stream);
 
 /* Learned warm start (no counterpart in the paper's method; it only changes the initial
  * vectors of the Eq. 6 solves): solves all sectors' right-hand sides at the n_train
@@ -249,7 +292,9 @@ void ccgf_set_autotune(int enable);
  * thread blocks (partial sums reduced by a second kernel), 200 the few-row kernel (one thread
  * per output column, for at most 8 rows and a short reduction), 100 the tensor-core kernel with A by TMA and B
  * staged by producer warps, 101 the register-fed tensor-core kernel, 102 the tensor-core kernel
- * with both operands by asynchronous copies (B from a pre-expanded image). */
+ * with both operands by asynchronous copies (B from a pre-expanded image), 300 the register-fed
+ * tensor-core kernel and 301 the tensor GEMM on a block kept only in FP64 (rounded as it is loaded),
+ * 400 a tensor GEMM (pair index maps) of a term formed from the density-fitting factors. */
 int ccgf_sigma_step_kernel(const ccgf_handle *h, int sector, int kshift, int step, ccgf_precision prec);
 
 /* Self-test of the bounded device waits (no counterpart in the paper): one warp allocates

@@ -42,7 +42,7 @@ class Stats(C.Structure):
                 ("warm_val_loss", C.c_double), ("warm_val_loss_baseline", C.c_double),
                 ("warm_rel_residual", C.c_double), ("warm_rel_residual_net", C.c_double),
                 ("warm_rel_residual_base", C.c_double), ("restart_used", C.c_longlong),
-                ("columns_per_batch", C.c_longlong)]
+                ("columns_per_batch", C.c_longlong), ("vector_ms", C.c_double), ("vector_bytes", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -51,6 +51,7 @@ class Stats(C.Structure):
 EXPORTS = ["ccgf_default_options", "ccgf_build_intermediates", "ccgf_dims", "ccgf_sigma_ip", "ccgf_sigma_ea",
            "ccgf_rhs", "ccgf_left", "ccgf_solve_gf", "ccgf_sigma_profile", "ccgf_sigma_step_name", "ccgf_sigma_ip_noalloc", "ccgf_launch_count",
            "ccgf_set_autotune", "ccgf_sigma_step_kernel", "ccgf_tensor_wait_selftest", "ccgf_inject_alloc_failure",
+           "ccgf_spectral_function", "ccgf_self_energy_correction", "ccgf_solve_gf_mor",
            "ccgf_train_warmstart", "ccgf_mlp_param_count", "ccgf_mlp_forward", "ccgf_mlp_loss_grad", "ccgf_destroy",
            "ccgf_status_string", "ccgf_last_error"]
 
@@ -100,6 +101,12 @@ def load(path: str | None = None):
     lib.ccgf_launch_count.restype = ll
     lib.ccgf_tensor_wait_selftest.argtypes = [C.c_double, vp]
     lib.ccgf_tensor_wait_selftest.restype = C.c_int
+    lib.ccgf_solve_gf_mor.argtypes = [vp, i, i, vp, i, vp, d, C.POINTER(Options), vp, i, C.POINTER(Stats), vp]
+    lib.ccgf_solve_gf_mor.restype = i
+    lib.ccgf_self_energy_correction.argtypes = [i, i, i, i, vp, vp, vp, vp, vp, vp]
+    lib.ccgf_self_energy_correction.restype = i
+    lib.ccgf_spectral_function.argtypes = [i, i, i, vp, vp, vp, vp, vp]
+    lib.ccgf_spectral_function.restype = i
     lib.ccgf_inject_alloc_failure.argtypes = [C.c_longlong]
     lib.ccgf_inject_alloc_failure.restype = None
     lib.ccgf_set_autotune.argtypes = [C.c_int]
@@ -231,6 +238,22 @@ def tensor_wait_selftest(limit_ms=50.0, stream=None):
     return int(load().ccgf_tensor_wait_selftest(float(limit_ms), _stream_ptr(stream)))
 
 
+def spectral_function(G, dos, G_minus=None, dos_total=None, stream=None):
+    """ccgf_spectral_function on device tensors: G [nk][nomega][nmo][nmo] complex128, dos [nk][nomega] float64."""
+    nk, nomega, nmo = G.shape[0], G.shape[1], G.shape[2]
+    return _check(load().ccgf_spectral_function(nk, nomega, nmo, _ptr(G), _ptr(G_minus), _ptr(dos), _ptr(dos_total),
+                                                _stream_ptr(stream)))
+
+
+def self_energy_correction(V, G_gw, G_gw_cas, G_cc_cas, G_out, stream=None):
+    """ccgf_self_energy_correction on device tensors (complex128): V [nk][nmo][nact], G_gw / G_out
+    [nk][nomega][nmo][nmo], G_gw_cas / G_cc_cas [nk][nomega][nact][nact]."""
+    nk, nomega, nmo = G_gw.shape[0], G_gw.shape[1], G_gw.shape[2]
+    nact = V.shape[2]
+    return _check(load().ccgf_self_energy_correction(nk, nomega, nmo, nact, _ptr(V), _ptr(G_gw), _ptr(G_gw_cas),
+                                                     _ptr(G_cc_cas), _ptr(G_out), _stream_ptr(stream)))
+
+
 def inject_alloc_failure(after):
     """ccgf_inject_alloc_failure: make the library's allocations fail after `after` more (-1 resets)."""
     load().ccgf_inject_alloc_failure(int(after))
@@ -290,6 +313,18 @@ def rhs(h: Handle, sector, K, p, out, stream=None):
 
 def left(h: Handle, sector, K, p, out, stream=None):
     return _check(load().ccgf_left(h.ptr, sector, K, p, _ptr(out), _stream_ptr(stream)))
+
+
+def solve_gf_mor(h: Handle, sectors, omega_mor, omega, eta, G_out, *, options=None, on_device=False, stream=None):
+    """Model-order-reduction G on the grid `omega` from solves at `omega_mor`; returns (status, stats dict)."""
+    om = np.ascontiguousarray(np.asarray(omega, dtype=np.float64))
+    omm = np.ascontiguousarray(np.asarray(omega_mor, dtype=np.float64))
+    st = Stats()
+    opt = options or default_options()
+    status = load().ccgf_solve_gf_mor(h.ptr, sectors, len(omm), omm.ctypes.data, len(om), om.ctypes.data, float(eta),
+                                      C.byref(opt), _ptr(G_out), 1 if on_device else 0, C.byref(st), _stream_ptr(stream))
+    _check(status, allow_not_converged=True)
+    return status, st.as_dict()
 
 
 def solve_gf(h: Handle, sectors, omega, eta, G_out, *, options=None, on_device=False, stream=None):

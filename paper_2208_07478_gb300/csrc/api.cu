@@ -224,6 +224,36 @@ ccgf_status ccgf_solve_gf(ccgf_handle *h, int sectors, int nomega, const double 
     return solve_gf(h, sectors, nomega, omega, eta, &o, G_out, G_on_device, stats, (cudaStream_t)stream);
 }
 
+ccgf_status ccgf_solve_gf_mor(ccgf_handle *h, int sectors, int n_mor, const double *omega_mor, int nomega, const double *omega,
+                              double eta, const ccgf_options *opt, double *G_out, int G_on_device, ccgf_stats *stats, void *stream) {
+    if (!h || !omega || !omega_mor || !G_out) { set_last_error("NULL handle, frequencies or output"); return CCGF_ERR_INVALID_ARG; }
+    if (sectors < 1 || sectors > 3 || nomega < 1 || n_mor < 1 || n_mor > 64) {
+        set_last_error("sectors must be 1..3, nomega >= 1 and 1 <= n_mor <= 64");
+        return CCGF_ERR_INVALID_ARG;
+    }
+    if (!(eta > 0.0) || !std::isfinite(eta)) { set_last_error("eta must be positive and finite"); return CCGF_ERR_INVALID_ARG; }
+    for (int w = 0; w < nomega; ++w)
+        if (!std::isfinite(omega[w])) { set_last_error("non-finite frequency"); return CCGF_ERR_NAN; }
+    for (int w = 0; w < n_mor; ++w)
+        if (!std::isfinite(omega_mor[w])) { set_last_error("non-finite model frequency"); return CCGF_ERR_NAN; }
+    ccgf_options o;
+    if (opt) o = *opt;
+    else ccgf_default_options(&o);
+    if (!(o.tol > 0.0) || o.restart_m < 2 || o.max_iter < 1 || o.max_refine < 1 || o.omega_chunk < 1 || o.kpoint < -1 ||
+        o.kpoint >= h->nk || !valid_wait(o.device_wait_timeout_ms)) {
+        set_last_error("invalid options");
+        return CCGF_ERR_INVALID_ARG;
+    }
+    if (o.prec != CCGF_FP64 && o.prec != CCGF_FP32 && o.prec != CCGF_TF32X3) { set_last_error("unknown precision"); return CCGF_ERR_INVALID_ARG; }
+    struct WaitScope {
+        ccgf_handle *h;
+        unsigned long long saved;
+        ~WaitScope() { h->wait_ns = saved; }
+    } scope{h, h->wait_ns};
+    h->wait_ns = wait_ns_of(o.device_wait_timeout_ms);
+    return solve_gf_mor(h, sectors, n_mor, omega_mor, nomega, omega, eta, &o, G_out, G_on_device, stats, (cudaStream_t)stream);
+}
+
 ccgf_status ccgf_sigma_profile(ccgf_handle *h, int sector, int kshift, long long nvec, const double *x, double *y,
                                ccgf_precision prec, void *stream, int max_steps, double *step_ms, double *step_flops,
                                int *nsteps) {

@@ -262,6 +262,11 @@ struct ccgf_handle {
     i64 launches = 0;
     // learned warm start (mlp.cu); capture of training solutions while ws_capturing
     WarmStart *ws = nullptr;
+    // model-order reduction (mor.cu): solutions of one (sector, K) kept as columns p * ncols_w + w
+    struct MorCapture {
+        int sector = 0, K = -1, nw = 0;
+        double2 *X = nullptr;   // [D][nmo * nw]
+    } mor_cap;
     bool ws_capturing = false;
     // bound of every tensor-core device wait (from ccgf_options::device_wait_timeout_ms)
     unsigned long long wait_ns = 1000000000ull;
@@ -318,8 +323,12 @@ ccgf_status warmstart_train(ccgf_handle *h, int sectors, int steps, i64 rows, do
                             cudaStream_t st);
 void warmstart_free(ccgf_handle *h);
 void warmstart_losses(const ccgf_handle *h, double *val_net, double *val_base);
+// solve.cu: copies the converged columns of one batch into the model-order-reduction capture
+void mor_capture_columns(ccgf_handle *h, const double2 *X, i64 D, int nv, int p0, int pend, int nw, int w0, cudaStream_t st);
 // solve.cu
 ccgf_status diag_estimate_device(ccgf_handle *h, int sector, int K, double *d, cudaStream_t st);
+ccgf_status solve_gf_mor(ccgf_handle *h, int sectors, int n_mor, const double *omega_mor, int nomega, const double *omega,
+                         double eta, const ccgf_options *opt, double *G_out, int G_on_device, ccgf_stats *stats, cudaStream_t st);
 ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omega, double eta,
                      const ccgf_options *opt, double *G_out, int G_on_device, ccgf_stats *stats,
                      cudaStream_t st);

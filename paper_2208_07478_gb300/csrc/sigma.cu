@@ -1268,7 +1268,14 @@ int plan_step_choice(const ccgf_handle *h, int sector, int K, int step, int pi) 
     const SigmaPlan *P = plan_of(h, sector, K);
     if (!P || step < 0 || step >= (int)P->steps.size() || pi < 0 || pi > 2) return -1;
     const SigmaStep &s = P->steps[step];
-    return s.kind == STEP_GEMM ? s.choice[pi] : -1;
+    if (s.kind == STEP_TGEMM) return 400;
+    if (s.kind != STEP_GEMM) return -1;
+    if (pi > 0 && !h->Wf[s.a_buf].p) {
+        // FP64-stored block (no FP32 copy): register-fed tensor cores or the tensor GEMM, rounding on load
+        GemmDesc d = s.g;
+        return (pi == 2 && tc_zgemm_supported(d)) ? 300 : 301;
+    }
+    return s.choice[pi];
 }
 
 void free_plans(ccgf_handle *h) {

@@ -140,6 +140,69 @@ __global__ void cgs_dot_kernel(const double2 *__restrict__ V, i64 vstride, const
     }
 }
 
+// Partial CGS dot products without atomics: a block of nv * ry threads (thread = column c, row lane y)
+// walks rows [b * rpb, (b + 1) * rpb) of the [D][nv] arrays, so a warp reads contiguous memory with
+// every lane busy whatever nv is; part[b][i][c] = sum over the block's rows of conj(V_i[mu][c]) w[mu][c].
+__global__ void __launch_bounds__(1024) ortho_dot_kernel(const double2 *__restrict__ V, i64 vstride, const double2 *__restrict__ w,
+                                                         double2 *__restrict__ part, int J, i64 D, int nv, int ry, i64 rpb) {
+    extern __shared__ double2 red[];                    // [ry][8][nv]
+    const int c = threadIdx.x % nv, y = threadIdx.x / nv;
+    const i64 r0 = (i64)blockIdx.x * rpb, r1 = min(D, r0 + rpb);
+    for (int i0 = 0; i0 < J; i0 += 8) {
+        double2 acc[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[k] = make_double2(0, 0);
+        if (y < ry)
+            for (i64 mu = r0 + y; mu < r1; mu += ry) {
+                const i64 t = mu * nv + c;
+                const double2 x = w[t];
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (i0 + k < J) {
+                        const double2 vv = V[(i64)(i0 + k) * vstride + t];
+                        acc[k].x += vv.x * x.x + vv.y * x.y;
+                        acc[k].y += vv.x * x.y - vv.y * x.x;
+                    }
+            }
+        if (y < ry)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) red[((i64)y * 8 + k) * nv + c] = acc[k];
+        __syncthreads();
+        for (int e = threadIdx.x; e < 8 * nv; e += blockDim.x) {
+            const int k = e / nv, cc = e % nv;
+            if (i0 + k < J) {
+                double2 sacc = make_double2(0, 0);
+                for (int yy = 0; yy < ry; ++yy) {
+                    const double2 q = red[((i64)yy * 8 + k) * nv + cc];
+                    sacc.x += q.x;
+                    sacc.y += q.y;
+                }
+                part[((i64)blockIdx.x * J + i0 + k) * nv + cc] = sacc;
+            }
+        }
+        __syncthreads();
+    }
+}
+// h[c][i] (+)= sum_b part[b][i][c]
+__global__ void ortho_sum_kernel(const double2 *__restrict__ part, int nblk, double2 *h, int hld, int J, int nv, int accumulate) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < J * nv; e += gridDim.x * blockDim.x) {
+        const int i = e / nv, c = e % nv;
+        double2 sacc = make_double2(0, 0);
+        for (int b = 0; b < nblk; ++b) {
+            const double2 q = part[((i64)b * J + i) * nv + c];
+            sacc.x += q.x;
+            sacc.y += q.y;
+        }
+        double2 *o = h + (i64)c * hld + i;
+        if (accumulate) {
+            o->x += sacc.x;
+            o->y += sacc.y;
+        } else {
+            *o = sacc;
+        }
+    }
+}
+
 // w[mu][c] -= sum_{i<J} h[c][i] V_i[mu][c]
 __global__ void cgs_axpy_kernel(const double2 *__restrict__ V, i64 vstride, double2 *w, const double2 *__restrict__ h, int hld,
                                 int J, i64 D, int nv) {
@@ -295,6 +358,27 @@ __global__ void scatter_g_kernel(int sector, const double2 *Ct, int N, int pend,
     }
 }
 
+// launch shape of ortho_dot_kernel: nv x ry threads (ry rows in flight per column, <= 1024 threads),
+// four blocks per SM, every block a contiguous range of rows
+struct OrthoGrid {
+    bool ok;   // false: nv > 256 (the atomic-reduction kernel runs instead)
+    unsigned nblk, threads;
+    int ry;
+    i64 rpb;
+    size_t smem;
+};
+inline OrthoGrid ortho_grid(i64 D, int nv) {
+    OrthoGrid g{};
+    g.ok = nv >= 1 && nv <= 256;
+    g.ry = std::max(1, 256 / std::max(1, nv));
+    g.threads = (unsigned)(nv * g.ry);
+    const i64 want = 152 * 4;
+    g.rpb = std::max<i64>(g.ry, ceil_div(D, want));
+    g.nblk = (unsigned)ceil_div(D, g.rpb);
+    g.smem = sizeof(double2) * 8 * (size_t)nv * g.ry;
+    return g;
+}
+
 inline unsigned g1(i64 n) {
     i64 g = ceil_div(n, 256);
     return (unsigned)std::max<i64>(1, std::min<i64>(g, 152 * 16));
@@ -315,7 +399,22 @@ __global__ void select_kernel(const int *mode, double2 *X, double2 *R, const dou
     }
 }
 
+// cap[mu][p * ncw + w0 + w] = X[mu][(p - p0) * nw + w] for the batch's orbitals p < pend
+__global__ void mor_copy_kernel(const double2 *__restrict__ X, i64 D, int nv, int p0, int pend, int nw, int w0, int N, int ncw,
+                                double2 *cap) {
+    for (i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x; t < D * nv; t += (i64)gridDim.x * blockDim.x) {
+        const i64 mu = t / nv;
+        const int c = (int)(t % nv), p = p0 + c / nw, w = c % nw;
+        if (p < pend) cap[mu * ((i64)N * ncw) + (i64)p * ncw + w0 + w] = X[t];
+    }
+}
+
 }  // namespace
+
+void mor_capture_columns(ccgf_handle *h, const double2 *X, i64 D, int nv, int p0, int pend, int nw, int w0, cudaStream_t st) {
+    mor_copy_kernel<<<g1(D * nv), 256, 0, st>>>(X, D, nv, p0, pend, nw, w0, h->n, h->mor_cap.nw, h->mor_cap.X);
+    h->launches++;
+}
 
 ccgf_status diag_estimate_device(ccgf_handle *h, int sector, int K, double *d, cudaStream_t st) {
     const i64 D = sector == CCGF_SECTOR_IP ? h->dim_ip : h->dim_ea;
@@ -340,13 +439,14 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
     ccgf_stats S{};
     double warm_rel_sum = 0, warm_net_sum = 0, warm_base_sum = 0;
     i64 warm_count = 0;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr, es0 = nullptr, es1 = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, es0 = nullptr, es1 = nullptr, ev2 = nullptr;
     int *nunconv_h = nullptr;
     auto cleanup = on_scope_exit([&] {
         if (nunconv_h) cudaFreeHost(nunconv_h);
-        for (cudaEvent_t e : {ev0, ev1, es0, es1})
+        for (cudaEvent_t e : {ev0, ev1, es0, es1, ev2})
             if (e) cudaEventDestroy(e);
     });
+    CCGF_CUDA_TRY(cudaEventCreate(&ev2));
     CCGF_CUDA_TRY(cudaEventCreate(&ev0));
     CCGF_CUDA_TRY(cudaEventCreate(&ev1));
     CCGF_CUDA_TRY(cudaEventCreate(&es0));
@@ -422,7 +522,7 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
         S.restart_used = m;
         S.columns_per_batch = std::max<long long>(S.columns_per_batch, (long long)np * nwc);
         const int nvmax = np * nwc;
-        DBuf<double2> Bq, E, B, X, R, U, AU, V, Ct, Hs, Hs2, Hm, cs, sn, g, y, z, Wk;
+        DBuf<double2> Bq, E, B, X, R, U, AU, V, Ct, Hs, Hs2, Hm, cs, sn, g, y, z, Wk, Op;
         DBuf<double> dvec, beta2, beta, hn2, target, res;
         DBuf<int> active, nunconv;
         CCGF_TRY(dalloc(Bq, D * N));
@@ -435,6 +535,7 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
         CCGF_TRY(dalloc(V, (i64)(m + 1) * D * nvmax));
         CCGF_TRY(dalloc(Ct, (i64)N * nvmax));
         CCGF_TRY(dalloc(Wk, (i64)304 * N * nvmax));
+        CCGF_TRY(dalloc(Op, (i64)608 * (m + 1) * nvmax));   // CGS partial sums (ortho_grid: at most 608 blocks)
         CCGF_TRY(dalloc(Hs, (i64)nvmax * (m + 1)));
         CCGF_TRY(dalloc(Hs2, (i64)nvmax * (m + 1)));
         CCGF_TRY(dalloc(Hm, (i64)nvmax * (m + 1) * m));
@@ -481,6 +582,7 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                 CCGF_CUDA_TRY(cudaMemcpyAsync(R.p, B.p, sizeof(double2) * Dn, cudaMemcpyDeviceToDevice, st));
                 const i64 rpb = std::max<i64>(64, ceil_div(D, std::max<i64>(1, 2048 / (i64)ceil_div(nv, 32))));
                 dim3 rgrid((unsigned)ceil_div(nv, 32), (unsigned)ceil_div(D, rpb));
+                const OrthoGrid og = ortho_grid(D, nv);
                 // target = tol * ||b||
                 CCGF_CUDA_TRY(cudaMemsetAsync(beta2.p, 0, sizeof(double) * nv, st));
                 colnorm2_kernel<<<rgrid, dim3(32, 8), 0, st>>>(B.p, beta2.p, D, nv, rpb);
@@ -575,30 +677,38 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                         if (opt->prec == CCGF_FP64) S.fp64_sigma_calls++; else S.lowp_sigma_calls++;
                         shift_kernel<<<g1(Dn), 256, 0, st>>>(Sh, U.p, AU.p, Vn, D, nv);
                         h->launches++;
-                        CCGF_CUDA_TRY(cudaMemsetAsync(Hs.p, 0, sizeof(double2) * nv * (m + 1), st));
                         for (int pass = 0; pass < 2; ++pass) {
-                            // CGS2: accumulate both passes' coefficients in Hs, subtract each pass
+                            // CGS2: pass 1 writes the coefficients into Hs, pass 2 into Hs2 and adds them to Hs;
+                            // each pass subtracts its own projection
                             DBuf<double2> &hp = pass == 0 ? Hs : Hs2;
-                            if (pass == 1) CCGF_CUDA_TRY(cudaMemsetAsync(Hs2.p, 0, sizeof(double2) * nv * (m + 1), st));
-                            cgs_dot_kernel<<<rgrid, dim3(32, 8), 0, st>>>(V.p, Dn, Vn, hp.p, m + 1, j + 1, D, nv, rpb);
-                            h->launches++;
+                            if (og.ok) {
+                                ortho_dot_kernel<<<og.nblk, og.threads, og.smem, st>>>(V.p, Dn, Vn, Op.p, j + 1, D, nv, og.ry,
+                                                                                    og.rpb);
+                                ortho_sum_kernel<<<(unsigned)ceil_div((i64)(j + 1) * nv, 256), 256, 0, st>>>(Op.p, og.nblk, hp.p,
+                                                                                                       m + 1, j + 1, nv, 0);
+                                h->launches += 2;
+                            } else {
+                                CCGF_CUDA_TRY(cudaMemsetAsync(hp.p, 0, sizeof(double2) * nv * (m + 1), st));
+                                cgs_dot_kernel<<<rgrid, dim3(32, 8), 0, st>>>(V.p, Dn, Vn, hp.p, m + 1, j + 1, D, nv, rpb);
+                                h->launches++;
+                            }
                             cgs_axpy_kernel<<<g1(Dn), 256, 0, st>>>(V.p, Dn, Vn, hp.p, m + 1, j + 1, D, nv);
                             h->launches++;
-                        }
-                        // sum the two CGS passes into Hs (small host-free kernel via permute-add)
-                        {
-                            PermDesc pd{};
-                            pd.nd = 1;
-                            pd.dims[0] = (i64)nv * (m + 1);
-                            pd.sA[0] = 1;
-                            pd.sC[0] = 1;
-                            pd.total = pd.dims[0];
-                            pd.batch = 1;
-                            pd.offA = h->zero_tab.p;
-                            pd.offC = h->zero_tab.p;
-                            pd.alpha = make_double2(1, 0);
-                            pd.beta = make_double2(1, 0);
-                            h->launches += launch_zpermute<double>(pd, Hs2.p, Hs.p, st);
+                            if (pass == 1) {
+                                // Hs += Hs2
+                                PermDesc pd{};
+                                pd.nd = 1;
+                                pd.dims[0] = (i64)nv * (m + 1);
+                                pd.sA[0] = 1;
+                                pd.sC[0] = 1;
+                                pd.total = pd.dims[0];
+                                pd.batch = 1;
+                                pd.offA = h->zero_tab.p;
+                                pd.offC = h->zero_tab.p;
+                                pd.alpha = make_double2(1, 0);
+                                pd.beta = make_double2(1, 0);
+                                h->launches += launch_zpermute<double>(pd, Hs2.p, Hs.p, st);
+                            }
                         }
                         CCGF_CUDA_TRY(cudaMemsetAsync(hn2.p, 0, sizeof(double) * nv, st));
                         colnorm2_kernel<<<rgrid, dim3(32, 8), 0, st>>>(Vn, hn2.p, D, nv, rpb);
@@ -609,11 +719,17 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                         h->launches++;
                         normalize_kernel<<<g1(Dn), 256, 0, st>>>(Vn, hn2.p, D, nv);
                         h->launches++;
+                        cudaEventRecord(ev2, st);
                         CCGF_CUDA_TRY(cudaMemcpyAsync(nunconv_h, nunconv.p, sizeof(int), cudaMemcpyDeviceToHost, st));
                         CCGF_CUDA_TRY(cudaStreamSynchronize(st));
-                        float ms = 0;
+                        float ms = 0, vms = 0;
                         cudaEventElapsedTime(&ms, es0, es1);
+                        cudaEventElapsedTime(&vms, es1, ev2);
                         sigma_ms += ms;
+                        // vector steps after the sigma: shift (3 vectors), two CGS passes (2 (J + 1) read
+                        // + 1 written each, twice), norm (1), normalisation (2) with J = j + 1 basis vectors
+                        S.vector_ms += vms;
+                        S.vector_bytes += 16.0 * (double)Dn * (4.0 * (j + 1) + 12.0);
                         J = j + 1;
                         it_total++;
                         // stop the cycle a little below the target so the FP64 check passes
@@ -630,6 +746,8 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                     h->launches++;
                 }
                 if (h->ws_capturing && np == N && NS == N) CCGF_TRY(warmstart_capture(h, sector, K, X.p, D, nw, w0, b2.data(), st));
+                if (h->mor_cap.X && h->mor_cap.sector == sector && h->mor_cap.K == K)
+                    mor_capture_columns(h, X.p, D, nv, p0, pend, nw, w0, st);
                 S.inner_iterations += it_total;
                 S.rhs_solved += (long long)std::min(np, pend - p0) * nw;
                 S.max_rel_residual = std::max(S.max_rel_residual, maxres);

@@ -267,3 +267,72 @@ def test_rows_oracle_vectors_equal_full_oracle():
             np.testing.assert_allclose(kr.rhs("ea", K, p), ke.rhs_ea(K, p), atol=1e-15)
             np.testing.assert_allclose(kr.left("ip", K, p), ke.left_ip(K, p), atol=1e-15)
             np.testing.assert_allclose(kr.left("ea", K, p), ke.left_ea(K, p), atol=1e-15)
+
+
+def test_dos_hartree_fock_lorentzians_and_sum_rule():
+    """HF limit: G_pp = 1/(w - e_p -+ i eta), so the retarded-convention DOS is a sum of Lorentzians
+    eta / pi / ((w - e_p)^2 + eta^2) (one per orbital); on a wide fine grid it integrates to nmo."""
+    from oracle.spectral import dos
+    s = make_system((2, 1, 1), 2, 3, 4, seed=5, L_sigma=0.0, t1_sigma=0.0, nomega=0)
+    z1, z2 = np.zeros_like(s.t1), np.zeros_like(s.t2)
+    ke = KEOM(s.kmesh, s.nocc, s.mo_energy, z1, z2, L=s.L, l1=z1, l2=z2)
+    eta = 0.05
+    w = np.linspace(-40.0, 40.0, 16001)
+    Gp = keom_gf(ke, w, eta, sectors=("ea",))
+    Gm = keom_gf(ke, w, eta, sectors=("ip",))
+    d = dos(Gp, Gm)
+    for K in range(s.nk):
+        ref = sum(eta / np.pi / ((w - e) ** 2 + eta ** 2) for e in s.mo_energy[K])
+        np.testing.assert_allclose(d[K], ref, rtol=1e-10, atol=1e-12)
+        integral = float(np.sum(0.5 * (d[K][1:] + d[K][:-1]) * np.diff(w)))
+        assert abs(integral - s.nmo) < 2e-3 * s.nmo
+    # the time-ordered trace alone is negative at the occupied levels
+    d_to = dos(Gp + Gm)
+    i_occ = np.argmin(np.abs(w - s.mo_energy[0, 0]))
+    assert d_to[0, i_occ] < 0 < d[0, i_occ]
+
+
+def test_self_energy_algebra_limits():
+    """Eqs. 12-14: equal GW and CC active-space G give back G_GW; a full active space (V unitary)
+    gives back the coupled-cluster G (rotated by V); Dyson form cross-check."""
+    from oracle.selfenergy import cc_gw
+    rng = np.random.default_rng(8)
+    nk, nw, n, m = 2, 3, 6, 3
+    c = lambda *sh: rng.normal(size=sh) + 1j * rng.normal(size=sh)
+    Ggw = c(nk, nw, n, n) + 4 * np.eye(n)
+    Q, _ = np.linalg.qr(c(n, n))
+    V = np.stack([Q[:, :m]] * nk)
+    Gcas = c(nk, nw, m, m) + 3 * np.eye(m)
+    np.testing.assert_allclose(cc_gw(V, Ggw, Gcas, Gcas), Ggw, atol=1e-12)
+    Vfull = np.stack([Q] * nk)
+    Gcc = c(nk, nw, n, n) + 3 * np.eye(n)
+    Ggw_cas = np.einsum('kia,kwij,kjb->kwab', Vfull.conj(), Ggw, Vfull)      # GW in the rotated basis
+    out = cc_gw(Vfull, Ggw, Ggw_cas, Gcc)
+    np.testing.assert_allclose(out, np.einsum('kia,kwab,kjb->kwij', Vfull, Gcc, Vfull.conj()), atol=1e-11)
+
+
+def test_mor_reproduces_model_frequencies_and_converges():
+    """MOR frequency interpolation: exact (up to rounding) at the model frequencies (Galerkin with the
+    solution in the subspace), and equal to the full G everywhere once the model frequencies span the
+    space the right-hand sides reach; with a few model points it interpolates a smooth G closely."""
+    from oracle.mor import mor_gf
+    s = make_system((2, 1, 1), 2, 3, 5, seed=41, L_sigma=0.05, t1_sigma=0.02, nomega=0)
+    ke = KEOM(s.kmesh, s.nocc, s.mo_energy, s.t1, s.t2, L=s.L)
+    eta = 0.05
+    grid = np.linspace(-1.0, 1.0, 41)
+    for kind in ("ip", "ea"):
+        A = ke.matrix(kind, 0)
+        n = s.nmo
+        Bm = np.stack([(ke.rhs_ip if kind == "ip" else ke.rhs_ea)(0, p) for p in range(n)], 1)
+        Em = np.stack([(ke.left_ip if kind == "ip" else ke.left_ea)(0, q) for q in range(n)], 0)
+        full = solvers.dense_gf(kind, A, Bm, Em, grid, eta)
+        wm = grid[::10]
+        G, r = mor_gf(kind, A, Bm, Em, wm, grid, eta, rel_tol=1e-10)
+        np.testing.assert_allclose(G[::10], full[::10], atol=1e-9 * np.abs(full).max())
+        np.testing.assert_allclose(G, full, atol=1e-6 * np.abs(full).max())     # 5 model points, smooth G
+        # enough model points to span every state the right-hand sides reach: exact on the whole grid
+        D = A.shape[0]
+        many = np.linspace(-3.0, 3.0, int(np.ceil(D / n)) + 4)
+        G2, r2 = mor_gf(kind, A, Bm, Em, many, grid, eta, rel_tol=1e-10)
+        assert r < r2 <= D
+        np.testing.assert_allclose(G2, full, atol=1e-9 * np.abs(full).max())
