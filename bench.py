@@ -205,6 +205,26 @@ def step_point(rank, world, step, nk, nomega, per_step):
     return idx % nk, (nomega // 2 + idx // nk) % nomega
 
 
+def vector_roofline(solver):
+    """Roofline of the Arnoldi vector steps (shift, CGS2, norm, normalisation): HBM bytes and FP64
+    flops against their peaks; the bound is the resource whose minimum time is longer."""
+    vms = solver.get("vector_ms") or 0.0
+    if vms <= 0:
+        return {"gbs": None}
+    hbm = measured_peaks().get("hbm_gbs", 6800.0)
+    t_hbm = solver["vector_bytes"] / (hbm * 1e9)
+    t_alu = solver["vector_flops"] / (FP64_PEAK_TFLOPS * 1e12)
+    bound = "hbm" if t_hbm >= t_alu else "alu"
+    t_min = max(t_hbm, t_alu)
+    return {"gbs": solver["vector_gbs"], "frac_of_hbm": round(solver["vector_gbs"] / hbm, 4),
+            "tflops_fp64": solver["vector_tflops"], "frac_of_fp64": round(solver["vector_tflops"] / FP64_PEAK_TFLOPS, 4),
+            "bound": bound, "frac_of_bound": round(t_min / (vms / 1e3), 4),
+            "peak_basis": "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs, of measured); FP64 SIMT "
+                          "152 x 2 DFMA x 2 x 2.07 GHz (derived, of nominal)",
+            "what": "shift, CGS2 dots and updates, norm, normalisation after every sigma: 16 (4J + 12) D nv bytes and "
+                    "(32 J + 14) D nv FP64 flops per Arnoldi step over CUDA-event time"}
+
+
 def gpu_arm(args):
     import torch
     from paper_2208_07478_gb300 import binding as B
@@ -292,7 +312,11 @@ def gpu_arm(args):
                 "columns_per_batch": max(int(x["columns_per_batch"]) for x in st),
                 "sigma_ms": round(sum(float(x["sigma_ms"]) for x in st), 2),
                 "vector_ms": round(vms, 2),
-                "vector_gbs": round(vbytes / (vms / 1e3) / 1e9, 1) if vms > 0 else None}
+                "refine_ms": round(sum(float(x["refine_ms"]) for x in st), 2),
+                "vector_gbs": round(vbytes / (vms / 1e3) / 1e9, 1) if vms > 0 else None,
+                "vector_tflops": (round(sum(float(x["vector_flops"]) for x in st) / (vms / 1e3) / 1e12, 4)
+                                  if vms > 0 else None),
+                "vector_bytes": vbytes, "vector_flops": sum(float(x["vector_flops"]) for x in st)}
 
     def sigma_roofline(prec):
         """Live per-step timing of one EA sigma (k = 0, nmo vectors) in form prec: the dominant kernel."""
@@ -369,12 +393,9 @@ def gpu_arm(args):
                      "what": f"build + {steps_grid:.0f} steps of this kind cover all nk x nomega x nmo^2 = {total_elems} G elements"},
            "roofline": roof, "sigma": sig, "gpu_launches": launches, "clocks": clk,
            "solver": solver_summary(st_v)}
-    out["vector_steps"] = {"gbs": out["solver"]["vector_gbs"],
-                           "frac_of_hbm": (round(out["solver"]["vector_gbs"] / measured_peaks().get("hbm_gbs", 6800.0), 4)
-                                           if out["solver"]["vector_gbs"] else None),
-                           "peak_basis": "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                           "what": "shift, CGS2 dots and updates, norm, normalisation after every sigma; algorithmic bytes "
-                                   "16 (4J + 12) D nv per Arnoldi step over CUDA-event time"}
+    out["vector_steps"] = vector_roofline(out["solver"])
+    for key in ("vector_bytes", "vector_flops"):
+        out["solver"].pop(key, None)
 
     if not args.no_chosen:
         other = {}

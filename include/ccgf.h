@@ -86,7 +86,11 @@ typedef struct {
     double tol;               /* relative residual ||b - M x|| / ||b|| per right-hand side */
     int restart_m;            /* GMRES restart length                                      */
     int max_iter;             /* cap on inner iterations per right-hand side              */
-    int max_refine;           /* cap on FP64 true-residual checks (refinement cycles)      */
+    int max_refine;           /* cap on GMRES cycles (restarts) per batch. With a low-
+                                 precision inner sigma a cycle that stops at the restart
+                                 length restarts from the low-precision residual; the FP64
+                                 true residual is taken when the iteration meets the target
+                                 (refinement step), and only it decides convergence      */
     int omega_chunk;          /* frequencies solved together per (sector, K) batch (at most;
                                  the solver splits batches that do not fit in device memory) */
     double device_wait_timeout_ms; /* bound of every tensor-core device wait, (0, 60000] ms;
@@ -112,9 +116,9 @@ typedef struct {
     long long rhs_solved;       /* right-hand sides solved                                */
     long long inner_iterations; /* sum over batches of GMRES iterations (batch-parallel)  */
     long long fp64_sigma_calls; /* FP64 sigma batches (true-residual recomputes)          */
-    long long lowp_sigma_calls; /* FP32 sigma batches                                     */
+    long long lowp_sigma_calls; /* low-precision sigma batches (iterations and restarts)   */
     double max_rel_residual;    /* largest final true relative residual                   */
-    double sigma_ms;            /* device time in sigma (CUDA events)                     */
+    double sigma_ms;            /* device time of the sigma calls inside Arnoldi steps    */
     double total_ms;            /* device time of the whole solve                         */
     long long kernel_launches;  /* kernels launched by the solve                          */
     long long warm_columns;     /* right-hand sides that started from the network's x0    */
@@ -133,6 +137,10 @@ typedef struct {
                                    (shift, both CGS passes, norm, normalisation)           */
     double vector_bytes;        /* their algorithmic HBM traffic: 16 (4J + 12) D nv bytes per
                                    step with J basis vectors (vector_bytes / vector_ms: GB/s) */
+    double refine_ms;           /* device time of the FP64 true-residual sigma calls       */
+    double vector_flops;        /* FP64 flops of the vector steps timed in vector_ms: (32 J + 14)
+                                   D nv per step (8 per complex multiply-add in both CGS passes,
+                                   shift 8, norm 4, normalisation 2)                        */
 } ccgf_stats;
 
 typedef struct ccgf_handle ccgf_handle;

@@ -42,7 +42,8 @@ class Stats(C.Structure):
                 ("warm_val_loss", C.c_double), ("warm_val_loss_baseline", C.c_double),
                 ("warm_rel_residual", C.c_double), ("warm_rel_residual_net", C.c_double),
                 ("warm_rel_residual_base", C.c_double), ("restart_used", C.c_longlong),
-                ("columns_per_batch", C.c_longlong), ("vector_ms", C.c_double), ("vector_bytes", C.c_double)]
+                ("columns_per_batch", C.c_longlong), ("vector_ms", C.c_double), ("vector_bytes", C.c_double),
+                ("refine_ms", C.c_double), ("vector_flops", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

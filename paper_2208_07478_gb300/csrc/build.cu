@@ -292,6 +292,24 @@ __global__ void uooov_kernel(Dims D, const double2 *G, double2 *out) {
     }
 }
 
+// U[km][ke][kn][m][e][n][f] = 2 (m e|n f) - (m f|n e)  (= 2<mn|ef> - <mn|fe>), kf = km - ke + kn
+__global__ void ovov_combo_kernel(Dims D, const double2 *G, double2 *U) {
+    const int o = D.o, v = D.v, nk = D.nk;
+    i64 total = (i64)nk * nk * nk * o * v * o * v;
+    GRID_STRIDE(idx, total) {
+        i64 r = idx;
+        int f = r % v; r /= v;
+        int nn = r % o; r /= o;
+        int e = r % v; r /= v;
+        int m = r % o; r /= o;
+        int kn = r % nk; r /= nk;
+        int ke = r % nk; r /= nk;
+        int km = (int)r;
+        int kf = kc3(D, km, ke, kn);
+        U[idx] = csub(cscale(G[idx], 2.0), ovov(D, G, km, kf, kn, m, f, nn, e));
+    }
+}
+
 // ring blocks from P = Wovvo and Qv = Wovov (both in the layout [kx][kj][km][j][x][m][e]):
 //   W1 = 2P - Qv, W2 = -P, WN = -Qv   (P, Qv are read from the W2 and WN slots)
 __global__ void ring_combine_kernel(double2 *W1, double2 *W2, double2 *WN, i64 n) {
@@ -587,16 +605,22 @@ ccgf_status build_intermediates(ccgf_handle *h, const ccgf_system *sys, const cc
         CCGF_TRY(G.run("Wovov bare", (int)o2, (int)v2, Q, 1, imap_pair(o, n, 1), Qmap, Qmap, imap_pair(v, n, 1),
                        imap_pair(o, v, v * o * v), imap_pair(v, ov, 1), Ld, lLd, Ld, lLd, W1, lW, aQ, bQ, oQ, 1.0, 0.0));
         // rows (m, e), columns (j, x), K (n, f) over every kn:
-        //   P += 2 (m e|n f) t[kj,kn,kx][j,n,x,f] - (m f|n e) t[kj,kn,kx][j,n,x,f] - (m e|n f) t[kj,kn,kf][j,n,f,x]
+        //   P += (2 (m e|n f) - (m f|n e)) t[kj,kn,kx][j,n,x,f] - (m e|n f) t[kj,kn,kf][j,n,f,x]
         //   Qv -= (m f|n e) t[kj,kn,kf][j,n,f,x]
         const IMap a_me = imap_pair(v, v * o * v, ov), a_nf = imap_pair(v, v, 1);
         const IMap a_me_x = imap_pair(v, v * o * v, 1), a_nf_x = imap_pair(v, v, ov);
         const IMap b_nf_1 = imap_pair(v, v2, 1), b_jx_1 = imap_pair(v, o * v2, v);
         const IMap b_nf_2 = imap_pair(v, v2, v), b_jx_2 = imap_pair(v, o * v2, 1);
-        CCGF_TRY(G.run("Wovvo t2 (1)", (int)ov, (int)ov, (int)ov, nk, a_me, a_nf, b_nf_1, b_jx_1, c_me, c_jx, OVOV, lOVOV, t2, lt2, W1,
-                       lW, a1, b1, oP, 2.0, 1.0));
-        CCGF_TRY(G.run("Wovvo t2 (2)", (int)ov, (int)ov, (int)ov, nk, a_me_x, a_nf_x, b_nf_1, b_jx_1, c_me, c_jx, OVOV, lOVOV, t2, lt2,
-                       W1, lW, a2, b1, oP, -1.0, 1.0));
+        {
+            // 2 (m e|n f) - (m f|n e) formed once (same layout as (m e|n f)), then one GEMM against t[kj,kn,kx]
+            DBuf<double2> U;
+            CCGF_TRY(dalloc(U, lOVOV));
+            ovov_combo_kernel<<<grid_for(lOVOV), 256, 0, st>>>(D, OVOV, U.p);
+            h->launches++;
+            CCGF_TRY(G.run("Wovvo t2 (1)", (int)ov, (int)ov, (int)ov, nk, a_me, a_nf, b_nf_1, b_jx_1, c_me, c_jx, U.p, U.n, t2, lt2,
+                           W1, lW, a1, b1, oP, 1.0, 1.0));
+            CCGF_CUDA_TRY(cudaStreamSynchronize(st));
+        }
         CCGF_TRY(G.run("Wovvo t2 (3)", (int)ov, (int)ov, (int)ov, nk, a_me, a_nf, b_nf_2, b_jx_2, c_me, c_jx, OVOV, lOVOV, t2, lt2, W1,
                        lW, a1, b2, oP, -1.0, 1.0));
         CCGF_TRY(G.run("Wovov t2", (int)ov, (int)ov, (int)ov, nk, a_me_x, a_nf_x, b_nf_2, b_jx_2, c_me, c_jx, OVOV, lOVOV, t2, lt2, W1,

@@ -120,11 +120,16 @@ struct TGemm {
     const i64 *offA, *offB, *offC;     // device tables: [batch * nred], [batch * nred], [batch]
     double2 alpha, beta;
 };
+// work: partial sums of the split over the contraction that a GEMM with few output tiles takes
+// (tgemm_workspace_elems; NULL or too small: no split)
 template <typename R>
 int launch_tgemm(const TGemm &d, const typename cvec<R>::T *A, const typename cvec<R>::T *B, typename cvec<R>::T *C,
-                 cudaStream_t st);
+                 cudaStream_t st, typename cvec<R>::T *work = nullptr, i64 work_elems = 0);
 // FP32 arithmetic on an FP64-stored A (rounded as it is loaded): operands without an FP32 copy
-int launch_tgemm_a64(const TGemm &d, const double2 *A, const float2 *B, float2 *C, cudaStream_t st);
+int launch_tgemm_a64(const TGemm &d, const double2 *A, const float2 *B, float2 *C, cudaStream_t st, float2 *work = nullptr,
+                     i64 work_elems = 0);
+int tgemm_ksplit(const TGemm &d);
+i64 tgemm_workspace_elems(const TGemm &d);
 struct GemmDesc;
 TGemm tgemm_of(const GemmDesc &g);
 
@@ -290,6 +295,7 @@ const char *plan_step_name(const ccgf_handle *h, int sector, int K, int step);
 ccgf_status sigma_apply(ccgf_handle *h, int sector, int K, int nv, const double2 *x, double2 *y,
                         ccgf_precision prec, cudaStream_t st);
 void free_plans(ccgf_handle *h);
+void release_caches(ccgf_handle *h);   // FP32 / TF32 copies, scratch arenas (rebuilt on demand)
 void set_autotune(bool on);
 int plan_step_choice(const ccgf_handle *h, int sector, int K, int step, int prec_index);
 // reads and clears the tensor-core error flag (synchronises st); CCGF_ERR_TIMEOUT when it was set

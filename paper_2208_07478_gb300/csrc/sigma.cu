@@ -926,7 +926,8 @@ int run_gemm_step(ccgf_handle *h, const SigmaPlan *P, const SigmaStep &s, int ch
         if (!A) {
             // no FP32 copy of this block (device memory): FP32 / TF32 arithmetic on the FP64 block
             if (tensor_cores && tc_zgemm_supported(d)) return launch_tc_zgemm_a64(d, h->W[s.a_buf].p, scr, C, h->tc_err.p, st);
-            return launch_tgemm_a64(tgemm_of(d), h->W[s.a_buf].p, scr, C, st);
+            return launch_tgemm_a64(tgemm_of(d), h->W[s.a_buf].p, scr, C, st, scr + P->seg[SEG_SPLITK],
+                                    P->seg[SEG_END] - P->seg[SEG_SPLITK]);
         }
     }
     if (choice == CHOICE_SMALLM) return launch_zgemm_smallm<R>(d, A, scr, C, st);
@@ -1118,7 +1119,10 @@ void run_plan(ccgf_handle *h, SigmaPlan *P, const double2 *x, double2 *y, cudaSt
         ++si;
         T *C = s.c_buf == BUF_Y ? yout : scr;
         if (s.kind == STEP_GEMM) {
-            h->launches += run_gemm_step<R>(h, P, s, s.choice[pi], tensor_cores, scr, yout, st);
+            int n = run_gemm_step<R>(h, P, s, s.choice[pi], tensor_cores, scr, yout, st);
+            // the measured choice may need operand copies released since (release_caches): default kernel
+            if (n == 0 && s.choice[pi] != 0) n = run_gemm_step<R>(h, P, s, 0, tensor_cores, scr, yout, st);
+            h->launches += n;
         } else if (s.kind == STEP_TGEMM) {
             auto ptr = [&](int b) -> T * {
                 if (b == BUF_Y) return yout;
@@ -1129,7 +1133,8 @@ void run_plan(ccgf_handle *h, SigmaPlan *P, const double2 *x, double2 *y, cudaSt
             d.offA = offs + s.offA_pos;
             d.offB = offs + s.offB_pos;
             d.offC = offs + s.offC_pos;
-            h->launches += launch_tgemm<R>(d, ptr(s.a_buf), ptr(s.b_buf), ptr(s.c_buf), st);
+            h->launches += launch_tgemm<R>(d, ptr(s.a_buf), ptr(s.b_buf), ptr(s.c_buf), st, scr + P->seg[SEG_SPLITK],
+                                           P->seg[SEG_END] - P->seg[SEG_SPLITK]);
         } else if (s.kind == STEP_PERM) {
             PermDesc d = s.p;
             d.offA = offs + s.offA_pos;
@@ -1278,6 +1283,22 @@ int plan_step_choice(const ccgf_handle *h, int sector, int K, int step, int pi) 
     return s.choice[pi];
 }
 
+// Drops what the handle keeps only for speed and rebuilds on demand: the FP32 copies of the
+// intermediates (ensure_fp32), their TF32 hi / lo splits (tc_prepare), the sigma scratch arenas, the
+// split-K workspaces and the ABI transposes. Synchronises the device (cudaFree).
+void release_caches(ccgf_handle *h) {
+    tc_free(h);
+    for (int b = 0; b < NBUF; ++b) dfree(h->Wf[b]);
+    h->fp32_done = false;
+    dfree(h->scratch);
+    dfree(h->scratch_f);
+    dfree(h->yf);
+    dfree(h->splitw64);
+    dfree(h->splitw32);
+    dfree(h->abi_x);
+    dfree(h->abi_y);
+}
+
 void free_plans(ccgf_handle *h) {
     for (SigmaPlan *p : h->plans)
         if (p) {
@@ -1415,7 +1436,7 @@ ccgf_status tc_error_check(ccgf_handle *h, cudaStream_t st) {
     CCGF_CUDA_TRY(cudaStreamSynchronize(st));
     if (flag) {
         CCGF_CUDA_TRY(cudaMemsetAsync(h->tc_err.p, 0, sizeof(int), st));
-        set_last_error("a tensor-core GEMM wait exceeded its 2 s limit; its output tile was not written");
+        set_last_error("a tensor-core GEMM wait exceeded its limit (ccgf_options::device_wait_timeout_ms); its output tile was not written");
         return CCGF_ERR_TIMEOUT;
     }
     return CCGF_OK;

@@ -5,10 +5,16 @@
 //   M_c = z_c + s A,  z_c = w_c - i eta, s = +1 (IP);   z_c = w_c + i eta, s = -1 (EA),
 // right-preconditioned by the diagonal P_c = 1 / (z_c + s d) with d the one-body part of diag(A).
 // The Krylov basis, the CGS2 orthogonalisation, the Hessenberg / Givens least squares and the
-// solution are FP64; the inner sigma runs in the requested precision; every restart recomputes the
-// true residual b - M x with the FP64 sigma, so a low-precision inner sigma becomes iterative
-// refinement. All loops are host-driven (one small device->host read per Arnoldi step): no device
-// code waits on anything.
+// solution are FP64; the inner sigma runs in the requested precision. With a low-precision inner
+// sigma a cycle that reaches the target of the low-precision iteration is followed by the FP64 true
+// residual b - M x (iterative refinement; only that residual decides convergence), a cycle cut by
+// the restart length restarts from the low-precision residual. All loops are host-driven (one
+// small device->host read per Arnoldi step): no device code waits on anything.
+//
+// On this part FP64 arithmetic (2 DFMA per SM and clock) rather than HBM bounds the vector steps:
+// a complex multiply-add on 16 bytes costs 4 DFMA, so the per-element kernels avoid FP64 division
+// (the preconditioner is a table made once per batch, normalisation multiplies by a reciprocal
+// per column) and 64-bit integer division (a thread keeps its column for the whole loop).
 #include "ccgf_internal.h"
 #include <algorithm>
 #include <cmath>
@@ -34,6 +40,14 @@ __device__ __forceinline__ double2 precond(const Shift &S, i64 mu, int c) {
     double2 z = S.z[c];
     return cdiv1(make_double2(z.x + S.s * S.d[mu], z.y));
 }
+
+// Per-element kernels over [D][nv] arrays: a block of cw * ry threads; thread (c0 = tid % cw,
+// y = tid / cw) takes columns c0, c0 + cw, ... of rows y, y + ry, ... of its block's row groups, so a
+// block reads ry * nv contiguous elements per group and no thread divides by nv in its loop.
+#define ROW_LOOP(D, nv, cw, ry)                                                                   \
+    const int c0_ = (int)threadIdx.x % (cw), y_ = (int)threadIdx.x / (cw);                        \
+    for (i64 mu = (i64)blockIdx.x * (ry) + y_; mu < (D); mu += (i64)gridDim.x * (ry))             \
+        for (int c = c0_; c < (nv); c += (cw))
 
 // diag estimate: IP r1 -Foo_ii, r2 Fvv_aa - Foo_ii - Foo_jj;  EA r1 Fvv_aa, r2 Fvv_aa + Fvv_bb - Foo_jj
 __global__ void diag_kernel(int sector, int K, int nk, int o, int v, const int *kadd, const int *ksub, const double2 *Foo,
@@ -183,34 +197,44 @@ __global__ void __launch_bounds__(1024) ortho_dot_kernel(const double2 *__restri
         __syncthreads();
     }
 }
-// h[c][i] (+)= sum_b part[b][i][c]
+// h[c][i] (+)= sum_b part[b][i][c]: one warp per (i, c), lanes over the blocks' partial sums (fixed
+// order, so the result does not depend on timing), then a shuffle reduction
 __global__ void ortho_sum_kernel(const double2 *__restrict__ part, int nblk, double2 *h, int hld, int J, int nv, int accumulate) {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < J * nv; e += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    for (int e = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); e < J * nv; e += (int)((gridDim.x * blockDim.x) >> 5)) {
         const int i = e / nv, c = e % nv;
         double2 sacc = make_double2(0, 0);
-        for (int b = 0; b < nblk; ++b) {
+        for (int b = lane; b < nblk; b += 32) {
             const double2 q = part[((i64)b * J + i) * nv + c];
             sacc.x += q.x;
             sacc.y += q.y;
         }
-        double2 *o = h + (i64)c * hld + i;
-        if (accumulate) {
-            o->x += sacc.x;
-            o->y += sacc.y;
-        } else {
-            *o = sacc;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            sacc.x += __shfl_xor_sync(0xffffffffu, sacc.x, off);
+            sacc.y += __shfl_xor_sync(0xffffffffu, sacc.y, off);
+        }
+        if (lane == 0) {
+            double2 *o = h + (i64)c * hld + i;
+            if (accumulate) {
+                o->x += sacc.x;
+                o->y += sacc.y;
+            } else {
+                *o = sacc;
+            }
         }
     }
 }
 
 // w[mu][c] -= sum_{i<J} h[c][i] V_i[mu][c]
 __global__ void cgs_axpy_kernel(const double2 *__restrict__ V, i64 vstride, double2 *w, const double2 *__restrict__ h, int hld,
-                                int J, i64 D, int nv) {
-    for (i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x; t < D * nv; t += (i64)gridDim.x * blockDim.x) {
-        int c = t % nv;
+                                int J, i64 D, int nv, int cw, int ry) {
+    ROW_LOOP(D, nv, cw, ry) {
+        const i64 t = mu * nv + c;
+        const double2 *hc = h + (i64)c * hld;
         double2 acc = w[t];
         for (int i = 0; i < J; ++i) {
-            double2 p = cmul(h[(i64)c * hld + i], V[(i64)i * vstride + t]);
+            const double2 p = cmul(hc[i], V[(i64)i * vstride + t]);
             acc.x -= p.x;
             acc.y -= p.y;
         }
@@ -218,59 +242,67 @@ __global__ void cgs_axpy_kernel(const double2 *__restrict__ V, i64 vstride, doub
     }
 }
 
+// preconditioner table P[mu][c] = 1 / (z_c + s d_mu), made once per batch
+__global__ void ptab_kernel(Shift S, double2 *P, i64 D, int nv, int cw, int ry) {
+    ROW_LOOP(D, nv, cw, ry) P[mu * nv + c] = precond(S, mu, c);
+}
 // U = P . V   (preconditioned direction)
-__global__ void precond_kernel(Shift S, const double2 *__restrict__ V, double2 *U, i64 D, int nv) {
-    for (i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x; t < D * nv; t += (i64)gridDim.x * blockDim.x) {
-        i64 mu = t / nv;
-        int c = t % nv;
-        U[t] = cmul(precond(S, mu, c), V[t]);
+__global__ void precond_kernel(const double2 *__restrict__ P, const double2 *__restrict__ V, double2 *U, i64 D, int nv, int cw,
+                               int ry) {
+    ROW_LOOP(D, nv, cw, ry) {
+        const i64 t = mu * nv + c;
+        U[t] = cmul(P[t], V[t]);
     }
 }
 // w = z U + s sigma(U)
-__global__ void shift_kernel(Shift S, const double2 *__restrict__ U, const double2 *__restrict__ AU, double2 *w, i64 D, int nv) {
-    for (i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x; t < D * nv; t += (i64)gridDim.x * blockDim.x) {
-        int c = t % nv;
-        double2 zu = cmul(S.z[c], U[t]);
-        double2 a = AU[t];
+__global__ void shift_kernel(Shift S, const double2 *__restrict__ U, const double2 *__restrict__ AU, double2 *w, i64 D, int nv,
+                             int cw, int ry) {
+    ROW_LOOP(D, nv, cw, ry) {
+        const i64 t = mu * nv + c;
+        const double2 zu = cmul(S.z[c], U[t]);
+        const double2 a = AU[t];
         w[t] = make_double2(zu.x + S.s * a.x, zu.y + S.s * a.y);
     }
 }
 // r = b - (z x + s sigma(x))
 __global__ void residual_kernel(Shift S, const double2 *__restrict__ b, const double2 *__restrict__ x,
-                                const double2 *__restrict__ Ax, double2 *r, i64 D, int nv) {
-    for (i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x; t < D * nv; t += (i64)gridDim.x * blockDim.x) {
-        int c = t % nv;
-        double2 zx = cmul(S.z[c], x[t]);
-        double2 a = Ax[t];
+                                const double2 *__restrict__ Ax, double2 *r, i64 D, int nv, int cw, int ry) {
+    ROW_LOOP(D, nv, cw, ry) {
+        const i64 t = mu * nv + c;
+        const double2 zx = cmul(S.z[c], x[t]);
+        const double2 a = Ax[t];
         r[t] = make_double2(b[t].x - zx.x - S.s * a.x, b[t].y - zx.y - S.s * a.y);
     }
 }
 // V0 = r / beta (0 where beta = 0 or the column is frozen)
-__global__ void start_kernel(const double2 *__restrict__ r, double2 *V0, const double *beta, const int *active, i64 D, int nv) {
-    for (i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x; t < D * nv; t += (i64)gridDim.x * blockDim.x) {
-        int c = t % nv;
-        double bb = beta[c];
+__global__ void start_kernel(const double2 *__restrict__ r, double2 *V0, const double *beta, const int *active, i64 D, int nv,
+                             int cw, int ry) {
+    ROW_LOOP(D, nv, cw, ry) {
+        const i64 t = mu * nv + c;
+        const double bb = beta[c];
         V0[t] = (active[c] && bb > 0) ? make_double2(r[t].x / bb, r[t].y / bb) : make_double2(0, 0);
     }
 }
-// V_{j+1} = w / hn
-__global__ void normalize_kernel(double2 *w, const double *hn2, i64 D, int nv) {
-    for (i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x; t < D * nv; t += (i64)gridDim.x * blockDim.x) {
-        int c = t % nv;
-        double hn = sqrt(hn2[c]);
-        w[t] = hn > 1e-300 ? make_double2(w[t].x / hn, w[t].y / hn) : make_double2(0, 0);
+// V_{j+1} = w / hn, as w * (1 / hn) with the reciprocal per column (ihn, from givens_kernel)
+__global__ void normalize_kernel(double2 *w, const double *ihn, i64 D, int nv, int cw, int ry) {
+    ROW_LOOP(D, nv, cw, ry) {
+        const i64 t = mu * nv + c;
+        const double r = ihn[c];
+        w[t] = make_double2(w[t].x * r, w[t].y * r);
     }
 }
 
 // Per column: new Hessenberg column j (CGS coefficients hsum, subdiagonal sqrt(hn2)), previous rotations,
 // new rotation, update g, count columns whose residual estimate is still above the target.
 __global__ void givens_kernel(int j, int m, int nv, const double2 *hsum, int hld, const double *hn2, double2 *H, double2 *cs,
-                              double2 *sn, double2 *g, const double *target, const int *active, double *res, int *nunconv) {
+                              double2 *sn, double2 *g, const double *target, const int *active, double *res, int *nunconv,
+                              double *ihn) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nv) return;
     double2 *Hc = H + (i64)c * (m + 1) * m;   // H[c][row][col], row < m+1, col < m
     for (int i = 0; i <= j; ++i) Hc[i * m + j] = hsum[(i64)c * hld + i];
     double hn = sqrt(hn2[c]);
+    ihn[c] = hn > 1e-300 ? 1.0 / hn : 0.0;
     Hc[(j + 1) * m + j] = make_double2(hn, 0);
     double2 *csc = cs + (i64)c * m, *snc = sn + (i64)c * m, *gc = g + (i64)c * (m + 1);
     for (int i = 0; i < j; ++i) {
@@ -317,18 +349,17 @@ __global__ void trisolve_kernel(int J, int m, int nv, const double2 *H, const do
         yc[i] = den > 0 ? cmul(s, cdiv1(d)) : make_double2(0, 0);
     }
 }
-__global__ void update_kernel(Shift S, int J, int m, const double2 *__restrict__ V, i64 vstride, const double2 *__restrict__ y,
-                              double2 *x, i64 D, int nv) {
-    for (i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x; t < D * nv; t += (i64)gridDim.x * blockDim.x) {
-        i64 mu = t / nv;
-        int c = t % nv;
+__global__ void update_kernel(const double2 *__restrict__ P, int J, int m, const double2 *__restrict__ V, i64 vstride,
+                              const double2 *__restrict__ y, double2 *x, i64 D, int nv, int cw, int ry) {
+    ROW_LOOP(D, nv, cw, ry) {
+        const i64 t = mu * nv + c;
         double2 acc = make_double2(0, 0);
         for (int i = 0; i < J; ++i) {
-            double2 p = cmul(y[(i64)c * m + i], V[(i64)i * vstride + t]);
+            const double2 p = cmul(y[(i64)c * m + i], V[(i64)i * vstride + t]);
             acc.x += p.x;
             acc.y += p.y;
         }
-        double2 u = cmul(precond(S, mu, c), acc);
+        const double2 u = cmul(P[t], acc);
         x[t].x += u.x;
         x[t].y += u.y;
     }
@@ -376,6 +407,21 @@ inline OrthoGrid ortho_grid(i64 D, int nv) {
     g.rpb = std::max<i64>(g.ry, ceil_div(D, want));
     g.nblk = (unsigned)ceil_div(D, g.rpb);
     g.smem = sizeof(double2) * 8 * (size_t)nv * g.ry;
+    return g;
+}
+
+// launch shape of the ROW_LOOP kernels: columns cw = min(nv, 1024), ry rows so a block has about 256
+// threads, eight blocks per SM (fewer for short arrays)
+struct RowGrid {
+    unsigned blocks, threads;
+    int cw, ry;
+};
+inline RowGrid row_grid(i64 D, int nv) {
+    RowGrid g{};
+    g.cw = std::max(1, std::min(nv, 1024));
+    g.ry = std::max(1, 256 / g.cw);
+    g.threads = (unsigned)(g.cw * g.ry);
+    g.blocks = (unsigned)std::max<i64>(1, std::min<i64>(ceil_div(D, g.ry), 152 * 8));
     return g;
 }
 
@@ -439,14 +485,17 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
     ccgf_stats S{};
     double warm_rel_sum = 0, warm_net_sum = 0, warm_base_sum = 0;
     i64 warm_count = 0;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr, es0 = nullptr, es1 = nullptr, ev2 = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, es0 = nullptr, es1 = nullptr, ev2 = nullptr, er0 = nullptr, er1 = nullptr;
+    bool refine_pending = false;   // er0 / er1 bracket an FP64 residual sigma not yet added to refine_ms
     int *nunconv_h = nullptr;
     auto cleanup = on_scope_exit([&] {
         if (nunconv_h) cudaFreeHost(nunconv_h);
-        for (cudaEvent_t e : {ev0, ev1, es0, es1, ev2})
+        for (cudaEvent_t e : {ev0, ev1, es0, es1, ev2, er0, er1})
             if (e) cudaEventDestroy(e);
     });
     CCGF_CUDA_TRY(cudaEventCreate(&ev2));
+    CCGF_CUDA_TRY(cudaEventCreate(&er0));
+    CCGF_CUDA_TRY(cudaEventCreate(&er1));
     CCGF_CUDA_TRY(cudaEventCreate(&ev0));
     CCGF_CUDA_TRY(cudaEventCreate(&ev1));
     CCGF_CUDA_TRY(cudaEventCreate(&es0));
@@ -468,8 +517,8 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
     double sigma_ms = 0;
 
     // Batch plan from the free device memory. Per column a batch holds the Krylov basis (m + 1
-    // vectors), five work vectors and its share of the sigma scratch (FP64, plus FP32 for a
-    // low-precision inner sigma). All orbitals x a frequency chunk form one batch when they fit;
+    // vectors), five work vectors, the preconditioner table and its share of the sigma scratch
+    // (FP64, plus FP32 for a low-precision inner sigma). All orbitals x a frequency chunk form one batch when they fit;
     // otherwise the restart length shrinks (not below 10), then the orbitals are split into chunks
     // of equal width (the last one padded with zero columns, so every batch reuses one sigma plan),
     // then the frequency chunk shrinks. Low-precision copies of the intermediates are decided first,
@@ -478,11 +527,15 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
     const bool lowp = opt->prec != CCGF_FP64;
     auto column_bytes = [&](i64 D, int mm) -> double {
         const double scratch = (double)sigma_scratch_per_column(h) * (16.0 + (lowp ? 8.0 : 0.0)) + (lowp ? 8.0 * D : 0.0);
-        return 16.0 * D * (mm + 6) + scratch + 16.0 * 304 * N;
+        return 16.0 * D * (mm + 7) + scratch + 16.0 * 304 * N;
     };
     {
         const int min_cols = std::min(NS * nwc, 16);
         const double reserve = column_bytes(Dmax_s, std::min(m_req, 20)) * min_cols + (double)(2ull << 30);
+        size_t fr = 0, tot = 0;
+        CCGF_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+        // copies made by earlier sigma calls (with a smaller reserve) give way to the solve's batch
+        if ((double)fr < reserve) release_caches(h);
         if (lowp) CCGF_TRY(ensure_fp32(h, st, (size_t)reserve));
         if (opt->prec == CCGF_TF32X3) {
             if (!h->tc_err.p) {
@@ -523,7 +576,8 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
         S.columns_per_batch = std::max<long long>(S.columns_per_batch, (long long)np * nwc);
         const int nvmax = np * nwc;
         DBuf<double2> Bq, E, B, X, R, U, AU, V, Ct, Hs, Hs2, Hm, cs, sn, g, y, z, Wk, Op;
-        DBuf<double> dvec, beta2, beta, hn2, target, res;
+        DBuf<double2> Pt;
+        DBuf<double> dvec, beta2, beta, hn2, ihn, target, res;
         DBuf<int> active, nunconv;
         CCGF_TRY(dalloc(Bq, D * N));
         CCGF_TRY(dalloc(E, (i64)N * D));
@@ -548,6 +602,8 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
         CCGF_TRY(dalloc(beta2, nvmax));
         CCGF_TRY(dalloc(beta, nvmax));
         CCGF_TRY(dalloc(hn2, nvmax));
+        CCGF_TRY(dalloc(ihn, nvmax));
+        CCGF_TRY(dalloc(Pt, D * nvmax));
         CCGF_TRY(dalloc(target, nvmax));
         CCGF_TRY(dalloc(res, nvmax));
         CCGF_TRY(dalloc(active, nvmax));
@@ -555,7 +611,8 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
         auto free_all = [&]() {
             DBuf<double2> *zb[] = {&Bq, &E, &B, &X, &R, &U, &AU, &V, &Ct, &Hs, &Hs2, &Hm, &cs, &sn, &g, &y, &z, &Wk};
             for (auto *b : zb) dfree(*b);
-            DBuf<double> *db[] = {&dvec, &beta2, &beta, &hn2, &target, &res};
+            dfree(Pt);
+            DBuf<double> *db[] = {&dvec, &beta2, &beta, &hn2, &ihn, &target, &res};
             for (auto *b : db) dfree(*b);
             dfree(active);
             dfree(nunconv);
@@ -576,6 +633,9 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                 for (int c = 0; c < nv; ++c) zh[c] = make_double2(omega[w0 + c % nw], sector == CCGF_SECTOR_IP ? -eta : eta);
                 CCGF_CUDA_TRY(cudaMemcpyAsync(z.p, zh.data(), sizeof(double2) * nv, cudaMemcpyHostToDevice, st));
                 Shift Sh{z.p, s, dvec.p};
+                const RowGrid rg = row_grid(D, nv);
+                ptab_kernel<<<rg.blocks, rg.threads, 0, st>>>(Sh, Pt.p, D, nv, rg.cw, rg.ry);
+                h->launches++;
                 expand_kernel<<<g1(Dn), 256, 0, st>>>(Bq.p, B.p, D, N, pend, p0, nw, nv);
                 h->launches++;
                 CCGF_CUDA_TRY(cudaMemsetAsync(X.p, 0, sizeof(double2) * Dn, st));
@@ -593,6 +653,7 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                 std::vector<double> tg(nv);
                 for (int c = 0; c < nv; ++c) tg[c] = tol * std::sqrt(b2[c]);
                 CCGF_CUDA_TRY(cudaMemcpyAsync(target.p, tg.data(), sizeof(double) * nv, cudaMemcpyHostToDevice, st));
+                bool warm_lowp = false;   // R from the warm start's residual in the low-precision form
                 if (opt->warm_start && np == N && NS == N) {
                     // learned initial vectors: per column keep the candidate (network, baseline, cold) with the
                     // smallest true residual; the cold start's residual is |b|
@@ -602,7 +663,7 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                         auto resid2 = [&](const double2 *x, double2 *r, std::vector<double> &out) -> ccgf_status {
                             CCGF_TRY(sigma_apply(h, sector, K, nv, x, AU.p, opt->prec, st));
                             if (opt->prec == CCGF_FP64) S.fp64_sigma_calls++; else S.lowp_sigma_calls++;
-                            residual_kernel<<<g1(Dn), 256, 0, st>>>(Sh, B.p, x, AU.p, r, D, nv);
+                            residual_kernel<<<rg.blocks, rg.threads, 0, st>>>(Sh, B.p, x, AU.p, r, D, nv, rg.cw, rg.ry);
                             h->launches++;
                             CCGF_CUDA_TRY(cudaMemsetAsync(beta2.p, 0, sizeof(double) * nv, st));
                             colnorm2_kernel<<<rgrid, dim3(32, 8), 0, st>>>(r, beta2.p, D, nv, rpb);
@@ -637,12 +698,27 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                         CCGF_CUDA_TRY(cudaMemcpyAsync(active.p, mode.data(), sizeof(int) * nv, cudaMemcpyHostToDevice, st));
                         select_kernel<<<g1(Dn), 256, 0, st>>>(active.p, X.p, R.p, U.p, V.p, B.p, D, nv);
                         h->launches++;
+                        warm_lowp = lowp;
                     }
                 }
                 i64 it_total = 0;
                 int cycles = 0;
                 bool converged = false;
                 double maxres = 0;
+                // R holds the FP64 true residual (else the residual of the low-precision operator: a GMRES
+                // restart that had not met the target yet)
+                bool r_fp64 = !warm_lowp;
+                auto true_residual = [&]() -> ccgf_status {
+                    cudaEventRecord(er0, st);
+                    CCGF_TRY(sigma_apply(h, sector, K, nv, X.p, AU.p, CCGF_FP64, st));
+                    cudaEventRecord(er1, st);
+                    refine_pending = true;
+                    S.fp64_sigma_calls++;
+                    residual_kernel<<<rg.blocks, rg.threads, 0, st>>>(Sh, B.p, X.p, AU.p, R.p, D, nv, rg.cw, rg.ry);
+                    h->launches++;
+                    r_fp64 = true;
+                    return CCGF_OK;
+                };
                 for (;;) {
                     // beta = ||r||, freeze columns already below target
                     CCGF_CUDA_TRY(cudaMemsetAsync(beta2.p, 0, sizeof(double) * nv, st));
@@ -653,6 +729,12 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                     std::vector<double> bh(nv);
                     CCGF_CUDA_TRY(cudaMemcpyAsync(bh.data(), beta.p, sizeof(double) * nv, cudaMemcpyDeviceToHost, st));
                     CCGF_CUDA_TRY(cudaStreamSynchronize(st));
+                    if (refine_pending) {
+                        float rms = 0;
+                        cudaEventElapsedTime(&rms, er0, er1);
+                        S.refine_ms += rms;
+                        refine_pending = false;
+                    }
                     int nact = 0;
                     maxres = 0;
                     for (int c = 0; c < nv; ++c) {
@@ -661,21 +743,27 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                         maxres = std::max(maxres, rr);
                         if (bh[c] > tg[c]) nact++;
                     }
+                    const bool stop = nact == 0 || cycles >= opt->max_refine || it_total >= opt->max_iter;
+                    if (stop && !r_fp64) {
+                        // decide (and report) on the FP64 true residual only
+                        CCGF_TRY(true_residual());
+                        continue;
+                    }
                     if (nact == 0) { converged = true; break; }
-                    if (cycles >= opt->max_refine || it_total >= opt->max_iter) break;
+                    if (stop) break;
                     cycles++;
-                    start_kernel<<<g1(Dn), 256, 0, st>>>(R.p, V.p, beta.p, active.p, D, nv);
+                    start_kernel<<<rg.blocks, rg.threads, 0, st>>>(R.p, V.p, beta.p, active.p, D, nv, rg.cw, rg.ry);
                     h->launches++;
                     int J = 0;
                     for (int j = 0; j < m; ++j) {
                         double2 *Vj = V.p + (i64)j * Dn, *Vn = V.p + (i64)(j + 1) * Dn;
-                        precond_kernel<<<g1(Dn), 256, 0, st>>>(Sh, Vj, U.p, D, nv);
+                        precond_kernel<<<rg.blocks, rg.threads, 0, st>>>(Pt.p, Vj, U.p, D, nv, rg.cw, rg.ry);
                         h->launches++;
                         cudaEventRecord(es0, st);
                         CCGF_TRY(sigma_apply(h, sector, K, nv, U.p, AU.p, opt->prec, st));
                         cudaEventRecord(es1, st);
                         if (opt->prec == CCGF_FP64) S.fp64_sigma_calls++; else S.lowp_sigma_calls++;
-                        shift_kernel<<<g1(Dn), 256, 0, st>>>(Sh, U.p, AU.p, Vn, D, nv);
+                        shift_kernel<<<rg.blocks, rg.threads, 0, st>>>(Sh, U.p, AU.p, Vn, D, nv, rg.cw, rg.ry);
                         h->launches++;
                         for (int pass = 0; pass < 2; ++pass) {
                             // CGS2: pass 1 writes the coefficients into Hs, pass 2 into Hs2 and adds them to Hs;
@@ -684,15 +772,15 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                             if (og.ok) {
                                 ortho_dot_kernel<<<og.nblk, og.threads, og.smem, st>>>(V.p, Dn, Vn, Op.p, j + 1, D, nv, og.ry,
                                                                                     og.rpb);
-                                ortho_sum_kernel<<<(unsigned)ceil_div((i64)(j + 1) * nv, 256), 256, 0, st>>>(Op.p, og.nblk, hp.p,
-                                                                                                       m + 1, j + 1, nv, 0);
+                                ortho_sum_kernel<<<(unsigned)ceil_div((i64)(j + 1) * nv, 8), 256, 0, st>>>(Op.p, og.nblk, hp.p, m + 1, j + 1,
+                                                                                                     nv, 0);
                                 h->launches += 2;
                             } else {
                                 CCGF_CUDA_TRY(cudaMemsetAsync(hp.p, 0, sizeof(double2) * nv * (m + 1), st));
                                 cgs_dot_kernel<<<rgrid, dim3(32, 8), 0, st>>>(V.p, Dn, Vn, hp.p, m + 1, j + 1, D, nv, rpb);
                                 h->launches++;
                             }
-                            cgs_axpy_kernel<<<g1(Dn), 256, 0, st>>>(V.p, Dn, Vn, hp.p, m + 1, j + 1, D, nv);
+                            cgs_axpy_kernel<<<rg.blocks, rg.threads, 0, st>>>(V.p, Dn, Vn, hp.p, m + 1, j + 1, D, nv, rg.cw, rg.ry);
                             h->launches++;
                             if (pass == 1) {
                                 // Hs += Hs2
@@ -715,9 +803,9 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                         h->launches++;
                         CCGF_CUDA_TRY(cudaMemsetAsync(nunconv.p, 0, sizeof(int), st));
                         givens_kernel<<<(unsigned)ceil_div(nv, 128), 128, 0, st>>>(j, m, nv, Hs.p, m + 1, hn2.p, Hm.p, cs.p, sn.p, g.p,
-                                                                                   target.p, active.p, res.p, nunconv.p);
+                                                                                   target.p, active.p, res.p, nunconv.p, ihn.p);
                         h->launches++;
-                        normalize_kernel<<<g1(Dn), 256, 0, st>>>(Vn, hn2.p, D, nv);
+                        normalize_kernel<<<rg.blocks, rg.threads, 0, st>>>(Vn, ihn.p, D, nv, rg.cw, rg.ry);
                         h->launches++;
                         cudaEventRecord(ev2, st);
                         CCGF_CUDA_TRY(cudaMemcpyAsync(nunconv_h, nunconv.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -730,6 +818,7 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                         // + 1 written each, twice), norm (1), normalisation (2) with J = j + 1 basis vectors
                         S.vector_ms += vms;
                         S.vector_bytes += 16.0 * (double)Dn * (4.0 * (j + 1) + 12.0);
+                        S.vector_flops += (double)Dn * (32.0 * (j + 1) + 14.0);
                         J = j + 1;
                         it_total++;
                         // stop the cycle a little below the target so the FP64 check passes
@@ -737,13 +826,20 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                     }
                     trisolve_kernel<<<(unsigned)ceil_div(nv, 128), 128, 0, st>>>(J, m, nv, Hm.p, g.p, y.p);
                     h->launches++;
-                    update_kernel<<<g1(Dn), 256, 0, st>>>(Sh, J, m, V.p, Dn, y.p, X.p, D, nv);
+                    update_kernel<<<rg.blocks, rg.threads, 0, st>>>(Pt.p, J, m, V.p, Dn, y.p, X.p, D, nv, rg.cw, rg.ry);
                     h->launches++;
-                    // true residual with the FP64 sigma (refinement step)
-                    CCGF_TRY(sigma_apply(h, sector, K, nv, X.p, AU.p, CCGF_FP64, st));
-                    S.fp64_sigma_calls++;
-                    residual_kernel<<<g1(Dn), 256, 0, st>>>(Sh, B.p, X.p, AU.p, R.p, D, nv);
-                    h->launches++;
+                    if (lowp && *nunconv_h != 0) {
+                        // the cycle ended at the restart length short of the target: restart from the
+                        // residual of the low-precision operator; the FP64 residual is taken once the
+                        // low-precision iteration meets the target (refinement step)
+                        CCGF_TRY(sigma_apply(h, sector, K, nv, X.p, AU.p, opt->prec, st));
+                        S.lowp_sigma_calls++;
+                        residual_kernel<<<rg.blocks, rg.threads, 0, st>>>(Sh, B.p, X.p, AU.p, R.p, D, nv, rg.cw, rg.ry);
+                        h->launches++;
+                        r_fp64 = false;
+                    } else {
+                        CCGF_TRY(true_residual());
+                    }
                 }
                 if (h->ws_capturing && np == N && NS == N) CCGF_TRY(warmstart_capture(h, sector, K, X.p, D, nw, w0, b2.data(), st));
                 if (h->mor_cap.X && h->mor_cap.sector == sector && h->mor_cap.K == K)

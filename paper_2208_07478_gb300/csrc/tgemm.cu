@@ -9,6 +9,7 @@
 // indices staged through shared memory per step. Each thread's row / column offsets are computed
 // once per tile; only the contraction index is decomposed per step.
 #include "ccgf_internal.h"
+#include <algorithm>
 
 namespace {
 
@@ -25,9 +26,13 @@ __device__ __forceinline__ float2 cvt2(float2 a, float2) { return a; }
 __device__ __forceinline__ float2 cvt2(double2 a, float2) { return make_float2((float)a.x, (float)a.y); }
 
 // TA: storage type of A (double2 with R = float: an FP64 operand rounded to FP32 as it is loaded)
+// ksplit > 1: grid z covers (batch, split); split s sums the reductions r in [s * rchunk, ...) (nred > 1)
+// or the contraction range [s * kchunk, ...) (nred = 1) and writes raw partial sums to
+// work[b][s][M][N]; tgemm_reduce_kernel applies alpha and beta.
 template <typename R, typename TA>
 __global__ void __launch_bounds__(256) tgemm_kernel(TGemm d, const TA *__restrict__ A, const typename cvec<R>::T *__restrict__ B,
-                                                    typename cvec<R>::T *__restrict__ C) {
+                                                    typename cvec<R>::T *__restrict__ C, int ksplit, int kchunk,
+                                                    typename cvec<R>::T *__restrict__ work) {
     typedef typename cvec<R>::T T;
     __shared__ T As[TK][TB + 1];
     __shared__ T Bs[TK][TB + 1];
@@ -49,22 +54,26 @@ __global__ void __launch_bounds__(256) tgemm_kernel(TGemm d, const TA *__restric
         b_coff[s] = n < d.N ? imap(d.bn, n) : -1;
     }
     const bool use_beta = d.beta.x != 0.0 || d.beta.y != 0.0;
-    for (int b = blockIdx.z; b < d.batch; b += gridDim.z) {
+    for (int bz = blockIdx.z; bz < d.batch * ksplit; bz += gridDim.z) {
+        const int b = bz / ksplit, ks = bz % ksplit;
+        const int rchunk = d.nred > 1 ? (d.nred + ksplit - 1) / ksplit : 1;
+        const int rbeg = d.nred > 1 ? ks * rchunk : 0, rend = d.nred > 1 ? min(d.nred, rbeg + rchunk) : 1;
+        const int kbeg = d.nred > 1 ? 0 : ks * kchunk, kend = d.nred > 1 ? d.K : min(d.K, kbeg + kchunk);
         T acc[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] = zero2<T>();
-        for (int r = 0; r < d.nred; ++r) {
+        for (int r = rbeg; r < rend; ++r) {
             const TA *Ab = A + d.offA[(i64)b * d.nred + r];
             const T *Bb = B + d.offB[(i64)b * d.nred + r];
-            for (int k0 = 0; k0 < d.K; k0 += TK) {
+            for (int k0 = kbeg; k0 < kend; k0 += TK) {
 #pragma unroll
                 for (int s = 0; s < 4; ++s) {
                     const int k = k0 + a_kk[s];
-                    As[a_kk[s]][a_row[s]] = (a_roff[s] >= 0 && k < d.K) ? cvt2(Ab[a_roff[s] + imap(d.ak, k)], T()) : zero2<T>();
+                    As[a_kk[s]][a_row[s]] = (a_roff[s] >= 0 && k < kend) ? cvt2(Ab[a_roff[s] + imap(d.ak, k)], T()) : zero2<T>();
                     const int kb = k0 + b_kk[s];
-                    Bs[b_kk[s]][b_col[s]] = (b_coff[s] >= 0 && kb < d.K) ? Bb[imap(d.bk, kb) + b_coff[s]] : zero2<T>();
+                    Bs[b_kk[s]][b_col[s]] = (b_coff[s] >= 0 && kb < kend) ? Bb[imap(d.bk, kb) + b_coff[s]] : zero2<T>();
                 }
                 __syncthreads();
 #pragma unroll
@@ -86,6 +95,20 @@ __global__ void __launch_bounds__(256) tgemm_kernel(TGemm d, const TA *__restric
                 }
                 __syncthreads();
             }
+        }
+        if (ksplit > 1) {
+            T *Wb = work + ((i64)b * ksplit + ks) * (i64)d.M * d.N;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int m = m0 + ty + 16 * i;
+                if (m >= d.M) continue;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int n = n0 + tx + 16 * j;
+                    if (n < d.N) Wb[(i64)m * d.N + n] = acc[i][j];
+                }
+            }
+            continue;
         }
         T *Cb = C + d.offC[b];
 #pragma unroll
@@ -112,28 +135,86 @@ __global__ void __launch_bounds__(256) tgemm_kernel(TGemm d, const TA *__restric
     }
 }
 
+template <typename R>
+__global__ void tgemm_reduce_kernel(TGemm d, int ksplit, const typename cvec<R>::T *__restrict__ work, typename cvec<R>::T *__restrict__ C) {
+    typedef typename cvec<R>::T T;
+    const i64 mn = (i64)d.M * d.N;
+    const bool use_beta = d.beta.x != 0.0 || d.beta.y != 0.0;
+    for (i64 t = (i64)blockIdx.x * blockDim.x + threadIdx.x; t < mn * d.batch; t += (i64)gridDim.x * blockDim.x) {
+        const int b = (int)(t / mn);
+        const i64 e = t - (i64)b * mn;
+        const int m = (int)(e / d.N), n = (int)(e - (i64)m * d.N);
+        R sx = 0, sy = 0;
+        for (int s = 0; s < ksplit; ++s) {
+            const T p = work[((i64)b * ksplit + s) * mn + e];
+            sx += p.x;
+            sy += p.y;
+        }
+        T *c = C + d.offC[b] + imap(d.cm, m) + imap(d.cn, n);
+        T v;
+        v.x = (R)d.alpha.x * sx - (R)d.alpha.y * sy;
+        v.y = (R)d.alpha.x * sy + (R)d.alpha.y * sx;
+        if (use_beta) {
+            const T o = *c;
+            v.x += (R)d.beta.x * o.x - (R)d.beta.y * o.y;
+            v.y += (R)d.beta.x * o.y + (R)d.beta.y * o.x;
+        }
+        *c = v;
+    }
+}
+
 }  // namespace
+
+// splits for a tensor GEMM whose output tiles cannot fill the GPU: enough (batch, split) blocks for two
+// waves, each keeping at least 64 contraction steps of work (1: no split)
+int tgemm_ksplit(const TGemm &d) {
+    const i64 tiles = ceil_div(d.M, TB) * ceil_div(d.N, TB) * (i64)d.batch;
+    if (tiles >= 304) return 1;
+    const i64 work = (i64)d.K * d.nred;
+    i64 s = ceil_div(304, tiles);
+    s = std::min<i64>(s, std::max<i64>(1, work / 1024));
+    if (d.nred > 1) s = std::min<i64>(s, d.nred);
+    else s = std::min<i64>(s, std::max<i64>(1, d.K / 64));
+    return (int)std::max<i64>(1, std::min<i64>(s, 64));
+}
+i64 tgemm_workspace_elems(const TGemm &d) {
+    const int s = tgemm_ksplit(d);
+    return s > 1 ? (i64)s * d.M * d.N * d.batch : 0;
+}
 
 IMap imap_single(i64 stride) { return IMap{1 << 30, 0, stride}; }
 IMap imap_pair(int inner, i64 outer_stride, i64 inner_stride) { return IMap{inner, outer_stride, inner_stride}; }
 
 template <typename R, typename TA>
-static int launch_t(const TGemm &d, const TA *A, const typename cvec<R>::T *B, typename cvec<R>::T *C, cudaStream_t st) {
+static int launch_t(const TGemm &d, const TA *A, const typename cvec<R>::T *B, typename cvec<R>::T *C, cudaStream_t st,
+                    typename cvec<R>::T *work, i64 work_elems) {
     if (d.batch <= 0 || d.M <= 0 || d.N <= 0 || d.nred <= 0) return 0;
-    const i64 z = d.batch < 65535 ? d.batch : 65535;
+    int ks = tgemm_ksplit(d);
+    if (ks > 1 && (!work || work_elems < tgemm_workspace_elems(d))) ks = 1;
+    int kchunk = d.K;
+    if (ks > 1 && d.nred == 1) {
+        kchunk = (int)(ceil_div(ceil_div(d.K, ks), TK) * TK);
+        ks = (int)ceil_div(d.K, kchunk);
+    } else if (ks > 1) {
+        ks = (int)ceil_div(d.nred, ceil_div(d.nred, ks));   // every split non-empty
+    }
+    const i64 zt = (i64)d.batch * ks, z = zt < 65535 ? zt : 65535;
     dim3 grid((unsigned)ceil_div(d.N, TB), (unsigned)ceil_div(d.M, TB), (unsigned)z);
-    tgemm_kernel<R, TA><<<grid, 256, 0, st>>>(d, A, B, C);
-    return 1;
+    tgemm_kernel<R, TA><<<grid, 256, 0, st>>>(d, A, B, C, ks, kchunk, work);
+    if (ks == 1) return 1;
+    const i64 n = (i64)d.M * d.N * d.batch, g = ceil_div(n, 256);
+    tgemm_reduce_kernel<R><<<(unsigned)(g > 4096 ? 4096 : g), 256, 0, st>>>(d, ks, work, C);
+    return 2;
 }
 template <typename R>
 int launch_tgemm(const TGemm &d, const typename cvec<R>::T *A, const typename cvec<R>::T *B, typename cvec<R>::T *C,
-                 cudaStream_t st) {
-    return launch_t<R, typename cvec<R>::T>(d, A, B, C, st);
+                 cudaStream_t st, typename cvec<R>::T *work, i64 work_elems) {
+    return launch_t<R, typename cvec<R>::T>(d, A, B, C, st, work, work_elems);
 }
-template int launch_tgemm<double>(const TGemm &, const double2 *, const double2 *, double2 *, cudaStream_t);
-template int launch_tgemm<float>(const TGemm &, const float2 *, const float2 *, float2 *, cudaStream_t);
-int launch_tgemm_a64(const TGemm &d, const double2 *A, const float2 *B, float2 *C, cudaStream_t st) {
-    return launch_t<float, double2>(d, A, B, C, st);
+template int launch_tgemm<double>(const TGemm &, const double2 *, const double2 *, double2 *, cudaStream_t, double2 *, i64);
+template int launch_tgemm<float>(const TGemm &, const float2 *, const float2 *, float2 *, cudaStream_t, float2 *, i64);
+int launch_tgemm_a64(const TGemm &d, const double2 *A, const float2 *B, float2 *C, cudaStream_t st, float2 *work, i64 work_elems) {
+    return launch_t<float, double2>(d, A, B, C, st, work, work_elems);
 }
 
 // a plain GemmDesc (single-stride indices) as a tensor GEMM

@@ -47,3 +47,39 @@ def test_frequency_walk_covers_the_grid_without_sharing():
             assert w not in seen
             seen[w] = rank
     assert sorted(seen) == list(range(nomega))
+
+
+def test_step_points_of_the_large_meshes_are_distinct():
+    """One (k, w) batch per step on the large meshes: every rank and step gets its own pair."""
+    nk, nomega, world = 27, 128, 4
+    seen = set()
+    for rank in range(world):
+        for step in range(40):
+            p = bench.step_point(rank, world, step, nk, nomega, "one_k")
+            assert 0 <= p[0] < nk and 0 <= p[1] < nomega
+            assert p not in seen
+            seen.add(p)
+    assert bench.step_point(0, 1, 5, 8, 64, "all_k") == (-1, 5)
+
+
+def test_every_workload_has_a_bench_profile():
+    from paper_2208_07478_gb300.synth import WORKLOADS
+    assert set(bench.PROFILE) == set(WORKLOADS)
+    assert bench.WORKLOAD in WORKLOADS
+
+
+def test_vector_roofline_names_the_binding_resource():
+    """The vector steps' bound is whichever of HBM bytes and FP64 flops needs the longer minimum time."""
+    hbm = bench.measured_peaks().get("hbm_gbs", 6800.0)
+    # 1 GB and 0.01 GFLOP in 1 ms: HBM-bound
+    s = {"vector_ms": 1.0, "vector_bytes": 1e9, "vector_flops": 1e7, "vector_gbs": 1e9 / 1e-3 / 1e9,
+         "vector_tflops": 1e7 / 1e-3 / 1e12}
+    r = bench.vector_roofline(s)
+    assert r["bound"] == "hbm"
+    assert abs(r["frac_of_bound"] - (1e9 / (hbm * 1e9)) / 1e-3) < 1e-4   # reported to 4 decimals
+    # 0.1 GB and 1 GFLOP in 1 ms: FP64-bound on this part
+    s = {"vector_ms": 1.0, "vector_bytes": 1e8, "vector_flops": 1e9, "vector_gbs": 100.0, "vector_tflops": 1.0}
+    r = bench.vector_roofline(s)
+    assert r["bound"] == "alu"
+    assert abs(r["frac_of_bound"] - (1e9 / (bench.FP64_PEAK_TFLOPS * 1e12)) / 1e-3) < 1e-4
+    assert bench.vector_roofline({"vector_ms": 0.0})["gbs"] is None
