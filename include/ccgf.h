@@ -90,7 +90,9 @@ typedef struct {
                                  precision inner sigma a cycle that stops at the restart
                                  length restarts from the low-precision residual; the FP64
                                  true residual is taken when the iteration meets the target
-                                 (refinement step), and only it decides convergence      */
+                                 (refinement step), and only it decides convergence; after
+                                 a failed check the low-precision iteration aims at a tenth
+                                 of the target                                            */
     int omega_chunk;          /* frequencies solved together per (sector, K) batch (at most;
                                  the solver splits batches that do not fit in device memory) */
     double device_wait_timeout_ms; /* bound of every tensor-core device wait, (0, 60000] ms;

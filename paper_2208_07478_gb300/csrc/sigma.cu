@@ -1363,21 +1363,33 @@ ccgf_status sigma_apply(ccgf_handle *h, int sector, int K, int nv, const double2
         if (h->scratch.n < P->scratch_elems) {
             CCGF_CUDA_TRY(cudaStreamSynchronize(st));
             dfree(h->scratch);
-            CCGF_TRY(dalloc(h->scratch, P->scratch_elems));
+            if (dalloc(h->scratch, P->scratch_elems) != CCGF_OK) {
+                // low-precision copies made by earlier calls give way to the FP64 scratch
+                release_caches(h);
+                CCGF_TRY(dalloc(h->scratch, P->scratch_elems));
+            }
         }
         if (autotune_enabled()) CCGF_TRY(autotune_plan<double>(h, P, 0, false, (double2 *)h->scratch.p, y, st));
         run_plan<double>(h, P, x, y, st);
     } else {
         if (h->scratch_f.n < P->scratch_elems || h->yf.n < D * nv) {
             CCGF_CUDA_TRY(cudaStreamSynchronize(st));
-            if (h->scratch_f.n < P->scratch_elems) {
-                dfree(h->scratch_f);
-                CCGF_TRY(dalloc(h->scratch_f, P->scratch_elems));
-            }
-            i64 dmax = h->dim_ip > h->dim_ea ? h->dim_ip : h->dim_ea;
-            if (h->yf.n < dmax * nv) {
-                dfree(h->yf);
-                CCGF_TRY(dalloc(h->yf, dmax * nv));
+            const i64 dmax = h->dim_ip > h->dim_ea ? h->dim_ip : h->dim_ea;
+            auto grow = [&]() -> ccgf_status {
+                if (h->scratch_f.n < P->scratch_elems) {
+                    dfree(h->scratch_f);
+                    CCGF_TRY(dalloc(h->scratch_f, P->scratch_elems));
+                }
+                if (h->yf.n < dmax * nv) {
+                    dfree(h->yf);
+                    CCGF_TRY(dalloc(h->yf, dmax * nv));
+                }
+                return CCGF_OK;
+            };
+            if (grow() != CCGF_OK) {
+                // copies made by earlier calls give way (they are made again below, as memory allows)
+                release_caches(h);
+                CCGF_TRY(grow());
             }
         }
         CCGF_TRY(ensure_fp32(h, st, (size_t)2 << 30));

@@ -7,8 +7,9 @@
 // The Krylov basis, the CGS2 orthogonalisation, the Hessenberg / Givens least squares and the
 // solution are FP64; the inner sigma runs in the requested precision. With a low-precision inner
 // sigma a cycle that reaches the target of the low-precision iteration is followed by the FP64 true
-// residual b - M x (iterative refinement; only that residual decides convergence), a cycle cut by
-// the restart length restarts from the low-precision residual. All loops are host-driven (one
+// residual b - M x (iterative refinement; only that residual decides convergence; once a check has
+// failed, the low-precision iteration aims at a tenth of the target), a cycle cut by the restart
+// length restarts from the low-precision residual. All loops are host-driven (one
 // small device->host read per Arnoldi step): no device code waits on anything.
 //
 // On this part FP64 arithmetic (2 DFMA per SM and clock) rather than HBM bounds the vector steps:
@@ -157,7 +158,25 @@ __global__ void cgs_dot_kernel(const double2 *__restrict__ V, i64 vstride, const
 // Partial CGS dot products without atomics: a block of nv * ry threads (thread = column c, row lane y)
 // walks rows [b * rpb, (b + 1) * rpb) of the [D][nv] arrays, so a warp reads contiguous memory with
 // every lane busy whatever nv is; part[b][i][c] = sum over the block's rows of conj(V_i[mu][c]) w[mu][c].
-__global__ void __launch_bounds__(1024) ortho_dot_kernel(const double2 *__restrict__ V, i64 vstride, const double2 *__restrict__ w,
+// rows [r0, r1) of one CGS chunk of NK basis vectors: acc[k] += conj(V_{i0+k}[mu][c]) w[mu][c]. NK is a
+// template argument so that exactly NK products run per element (a predicated product still
+// occupies the FP64 pipe, which bounds these kernels on this part).
+template <int NK>
+__device__ __forceinline__ void dot_rows(const double2 *__restrict__ V, i64 vstride, const double2 *__restrict__ w, int i0, i64 r0,
+                                         i64 r1, int y, int ry, int nv, int c, double2 (&acc)[8]) {
+    for (i64 mu = r0 + y; mu < r1; mu += ry) {
+        const i64 t = mu * nv + c;
+        const double2 x = w[t];
+#pragma unroll
+        for (int k = 0; k < NK; ++k) {
+            const double2 vv = V[(i64)(i0 + k) * vstride + t];
+            acc[k].x += vv.x * x.x + vv.y * x.y;
+            acc[k].y += vv.x * x.y - vv.y * x.x;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) ortho_dot_kernel(const double2 *__restrict__ V, i64 vstride, const double2 *__restrict__ w,
                                                          double2 *__restrict__ part, int J, i64 D, int nv, int ry, i64 rpb) {
     extern __shared__ double2 red[];                    // [ry][8][nv]
     const int c = threadIdx.x % nv, y = threadIdx.x / nv;
@@ -166,18 +185,18 @@ __global__ void __launch_bounds__(1024) ortho_dot_kernel(const double2 *__restri
         double2 acc[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) acc[k] = make_double2(0, 0);
-        if (y < ry)
-            for (i64 mu = r0 + y; mu < r1; mu += ry) {
-                const i64 t = mu * nv + c;
-                const double2 x = w[t];
-#pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    if (i0 + k < J) {
-                        const double2 vv = V[(i64)(i0 + k) * vstride + t];
-                        acc[k].x += vv.x * x.x + vv.y * x.y;
-                        acc[k].y += vv.x * x.y - vv.y * x.x;
-                    }
+        if (y < ry) {
+            switch (min(8, J - i0)) {
+            case 1: dot_rows<1>(V, vstride, w, i0, r0, r1, y, ry, nv, c, acc); break;
+            case 2: dot_rows<2>(V, vstride, w, i0, r0, r1, y, ry, nv, c, acc); break;
+            case 3: dot_rows<3>(V, vstride, w, i0, r0, r1, y, ry, nv, c, acc); break;
+            case 4: dot_rows<4>(V, vstride, w, i0, r0, r1, y, ry, nv, c, acc); break;
+            case 5: dot_rows<5>(V, vstride, w, i0, r0, r1, y, ry, nv, c, acc); break;
+            case 6: dot_rows<6>(V, vstride, w, i0, r0, r1, y, ry, nv, c, acc); break;
+            case 7: dot_rows<7>(V, vstride, w, i0, r0, r1, y, ry, nv, c, acc); break;
+            default: dot_rows<8>(V, vstride, w, i0, r0, r1, y, ry, nv, c, acc); break;
             }
+        }
         if (y < ry)
 #pragma unroll
             for (int k = 0; k < 8; ++k) red[((i64)y * 8 + k) * nv + c] = acc[k];
@@ -389,7 +408,7 @@ __global__ void scatter_g_kernel(int sector, const double2 *Ct, int N, int pend,
     }
 }
 
-// launch shape of ortho_dot_kernel: nv x ry threads (ry rows in flight per column, <= 1024 threads),
+// launch shape of ortho_dot_kernel: nv x ry threads (ry rows in flight per column, <= 256 threads),
 // four blocks per SM, every block a contiguous range of rows
 struct OrthoGrid {
     bool ok;   // false: nv > 256 (the atomic-reduction kernel runs instead)
@@ -531,7 +550,9 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
     };
     {
         const int min_cols = std::min(NS * nwc, 16);
-        const double reserve = column_bytes(Dmax_s, std::min(m_req, 20)) * min_cols + (double)(2ull << 30);
+        // the sector loop's fixed share (right-hand / left vectors, a 4 GB margin) plus a small batch
+        const double fixed = (double)(4ull << 30) + 32.0 * Dmax_s * N;
+        const double reserve = fixed + column_bytes(Dmax_s, std::min(m_req, 20)) * min_cols + (double)(2ull << 30);
         size_t fr = 0, tot = 0;
         CCGF_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
         // copies made by earlier sigma calls (with a smaller reserve) give way to the solve's batch
@@ -708,6 +729,8 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                 // R holds the FP64 true residual (else the residual of the low-precision operator: a GMRES
                 // restart that had not met the target yet)
                 bool r_fp64 = !warm_lowp;
+                bool tightened = false;
+                std::vector<double> tg_inner(nv);
                 auto true_residual = [&]() -> ccgf_status {
                     cudaEventRecord(er0, st);
                     CCGF_TRY(sigma_apply(h, sector, K, nv, X.p, AU.p, CCGF_FP64, st));
@@ -751,6 +774,16 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                     }
                     if (nact == 0) { converged = true; break; }
                     if (stop) break;
+                    if (lowp && r_fp64 && cycles > 0 && !tightened) {
+                        // the FP64 check failed after a low-precision iteration that had met the target:
+                        // from here on that iteration aims a decade lower, so that the next check is not
+                        // decided by the low-precision operator's rounding (one refinement step instead
+                        // of many that each gain little)
+                        for (int c = 0; c < nv; ++c) tg_inner[c] = 0.1 * tg[c];
+                        CCGF_CUDA_TRY(cudaMemcpyAsync(target.p, tg_inner.data(), sizeof(double) * nv, cudaMemcpyHostToDevice, st));
+                        tightened = true;
+                        continue;
+                    }
                     cycles++;
                     start_kernel<<<rg.blocks, rg.threads, 0, st>>>(R.p, V.p, beta.p, active.p, D, nv, rg.cw, rg.ry);
                     h->launches++;

@@ -152,6 +152,42 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_zgemm_kernel(GemmDesc d, const
     const uint32_t idesc = make_idesc(NR);
     int issued = 0;
 
+    // The operands of stage kt + 1 are loaded into registers (A rounded to FP32 on load) right after
+    // stage kt is split into shared memory, so their global-load latency overlaps the tensor cores'
+    // work on stage kt instead of following it. 32 A tasks (8 rows x 8 complex k) and at most 32 B
+    // tasks (4 complex n x 16 complex k): four of each per warp.
+    float2 ra[4][2], rb[4][2];
+    auto load_regs = [&](int kt) {
+        const int r = kt / ktiles, k0 = (kt % ktiles) * BKC;
+        const TA *Ab = A + d.offA[(i64)b * d.nred + r];
+        const float2 *Bb = B + d.offB[(i64)b * d.nred + r];
+        const int r8 = lane & 7, c = lane >> 3, nl = lane & 3, kp = lane >> 2;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int t = warp + q * (NTHREADS / 32);
+            const int g = t >> 1, kh = t & 1;
+            const int m = m0 + g * 8 + r8, k = k0 + kh * 8 + c * 2;
+            float2 v0 = make_float2(0.f, 0.f), v1 = v0;
+            if (m < d.M) {
+                const TA *row = Ab + (i64)m * d.rsA;
+                if (k < d.K) v0 = as_f2(row[(i64)k * d.csA]);
+                if (k + 1 < d.K) v1 = as_f2(row[(i64)(k + 1) * d.csA]);
+            }
+            ra[q][0] = v0;
+            ra[q][1] = v1;
+            float2 u0 = make_float2(0.f, 0.f), u1 = u0;
+            const int n = n0 + t * 4 + nl, kb = k0 + kp * 2;
+            if (t < BNc / 4 && n < d.N) {
+                const float2 *col = Bb + (i64)n * d.csB;
+                if (kb < d.K) u0 = col[(i64)kb * d.rsB];
+                if (kb + 1 < d.K) u1 = col[(i64)(kb + 1) * d.rsB];
+            }
+            rb[q][0] = u0;
+            rb[q][1] = u1;
+        }
+    };
+    if (total > 0) load_regs(0);
+
     for (int kt = 0; kt < total; ++kt) {
         const int st = kt & 1;
         if (kt >= 2 && !mbar_wait(&bars[st], ((kt - 2) >> 1) & 1, d.wait_ns)) {
@@ -161,52 +197,38 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_zgemm_kernel(GemmDesc d, const
         }
         __syncthreads();
         if (abort_flag) break;
-        const int r = kt / ktiles, k0 = (kt % ktiles) * BKC;
-        const TA *Ab = A + d.offA[(i64)b * d.nred + r];
-        const float2 *Bb = B + d.offB[(i64)b * d.nred + r];
         unsigned char *sAh = smem_raw + st * stage_bytes, *sAl = sAh + a_bytes, *sBh = sAl + a_bytes, *sBl = sBh + b_bytes;
-
-        // A: 32 warp tasks of 8 rows x 8 complex k; lane = (row r8, pair c) writes one 16-byte chunk
-        // (2 complex k) of core matrix (group g, K index kh*4 + c) in the hi and lo tiles
         {
+            // A: lane = (row r8, pair c) writes one 16-byte chunk (2 complex k) of core matrix (group g,
+            // K index kh*4 + c) in the hi and lo tiles
             const int r8 = lane & 7, c = lane >> 3;
-            for (int t = warp; t < 32; t += NTHREADS / 32) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int t = warp + q * (NTHREADS / 32);
                 const int g = t >> 1, kh = t & 1;
-                const int m = m0 + g * 8 + r8, k = k0 + kh * 8 + c * 2;
-                float2 v0 = make_float2(0.f, 0.f), v1 = v0;
-                if (m < d.M) {
-                    const TA *row = Ab + (i64)m * d.rsA;
-                    if (k < d.K) v0 = as_f2(row[(i64)k * d.csA]);
-                    if (k + 1 < d.K) v1 = as_f2(row[(i64)(k + 1) * d.csA]);
-                }
                 float h0, l0, h1, l1, h2, l2, h3, l3;
-                split(v0.x, h0, l0);
-                split(v0.y, h1, l1);
-                split(v1.x, h2, l2);
-                split(v1.y, h3, l3);
+                split(ra[q][0].x, h0, l0);
+                split(ra[q][0].y, h1, l1);
+                split(ra[q][1].x, h2, l2);
+                split(ra[q][1].y, h3, l3);
                 const uint32_t off = g * 1024 + (kh * 4 + c) * 128 + r8 * 16;
                 st_shared4(sAh + off, h0, h1, h2, h3);
                 st_shared4(sAl + off, l0, l1, l2, l3);
             }
         }
-        // B': BNc / 4 warp tasks of 4 complex n (8 real rows = one core-matrix group) x 16 complex k;
-        // lane = (n nl, k pair kp) writes rows 2nl and 2nl+1 of core matrix kp, odd kp starting with
-        // the second row so that the 8 lanes of each store phase hit distinct banks
         {
+            // B': lane = (n nl, k pair kp) writes rows 2nl and 2nl+1 of core matrix kp, odd kp starting
+            // with the second row so that the 8 lanes of each store phase hit distinct banks
             const int nl = lane & 3, kp = lane >> 2;
-            for (int t = warp; t < BNc / 4; t += NTHREADS / 32) {
-                const int n = n0 + t * 4 + nl, k = k0 + kp * 2;
-                float2 v0 = make_float2(0.f, 0.f), v1 = v0;
-                if (n < d.N) {
-                    const float2 *col = Bb + (i64)n * d.csB;
-                    if (k < d.K) v0 = col[(i64)k * d.rsB];
-                    if (k + 1 < d.K) v1 = col[(i64)(k + 1) * d.rsB];
-                }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int t = warp + q * (NTHREADS / 32);
+                if (t >= BNc / 4) continue;
                 float rh0, rl0, ih0, il0, rh1, rl1, ih1, il1;
-                split(v0.x, rh0, rl0);
-                split(v0.y, ih0, il0);
-                split(v1.x, rh1, rl1);
-                split(v1.y, ih1, il1);
+                split(rb[q][0].x, rh0, rl0);
+                split(rb[q][0].y, ih0, il0);
+                split(rb[q][1].x, rh1, rl1);
+                split(rb[q][1].y, ih1, il1);
                 const uint32_t base = t * 1024 + kp * 128 + (2 * nl) * 16;
                 const uint32_t o_re = base, o_im = base + 16;   // row 2n: (Re, -Im), row 2n+1: (Im, Re)
                 if (kp & 1) {
@@ -222,6 +244,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_zgemm_kernel(GemmDesc d, const
                 }
             }
         }
+        if (kt + 1 < total) load_regs(kt + 1);
         // generic-proxy shared stores -> visible to the tensor core (async proxy)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
@@ -868,8 +891,9 @@ size_t tc_zgemm_smem_bytes(int BNc) {
 
 template <typename TA>
 static int launch_tc_reg(const GemmDesc &d, const TA *A, const float2 *B, float2 *C, int *err, cudaStream_t st) {
-    // complex N tile: 128 (256 real TMEM columns), or N rounded up to a multiple of 8 when smaller
-    const int BNc = d.N >= 128 ? 128 : (int)ceil_div(d.N, 8) * 8;
+    // complex N tile: N split evenly into tiles of at most 128 (256 real TMEM columns), each a multiple of 8
+    const i64 ntiles = ceil_div(d.N, 128);
+    const int BNc = (int)(ceil_div(ceil_div(d.N, ntiles), 8) * 8);
     const int NR = 2 * BNc;
     const size_t smem = tc_zgemm_smem_bytes(BNc);
     const dim3 grid((unsigned)ceil_div(d.N, BNc), (unsigned)ceil_div(d.M, BM), (unsigned)d.batch);

@@ -7,7 +7,9 @@
 //
 // Tile: 64 x 64 complex outputs per CTA, 256 threads with 4 x 4 outputs each, 16 contraction
 // indices staged through shared memory per step. Each thread's row / column offsets are computed
-// once per tile; only the contraction index is decomposed per step.
+// once per tile; its contraction index is kept as (i / d2, i % d2) and advanced by 16 per step with
+// two additions and a compare (no division in the loop: in FP32 the index arithmetic would
+// otherwise cost as much as the multiply-adds).
 #include "ccgf_internal.h"
 #include <algorithm>
 
@@ -16,6 +18,24 @@ namespace {
 constexpr int TB = 64, TK = 16;
 
 __device__ __forceinline__ i64 imap(const IMap &m, i64 i) { return (i / m.d2) * m.s1 + (i % m.d2) * m.s2; }
+
+// contraction index k < 2^31 of an IMap as (q, r) = (k / d2, k % d2), advanced by TK per step
+struct KPos {
+    int q, r;
+};
+__device__ __forceinline__ KPos kpos(const IMap &m, int k) {
+    const int q = k / m.d2;
+    return KPos{q, k - q * m.d2};
+}
+__device__ __forceinline__ void kadvance(const IMap &m, int q16, int r16, KPos &p) {
+    p.r += r16;
+    p.q += q16;
+    if (p.r >= m.d2) {
+        p.r -= m.d2;
+        ++p.q;
+    }
+}
+__device__ __forceinline__ i64 koff(const IMap &m, const KPos &p) { return (i64)p.q * m.s1 + (i64)p.r * m.s2; }
 
 template <typename T> __device__ __forceinline__ T zero2();
 template <> __device__ __forceinline__ double2 zero2<double2>() { return make_double2(0.0, 0.0); }
@@ -54,6 +74,7 @@ __global__ void __launch_bounds__(256) tgemm_kernel(TGemm d, const TA *__restric
         b_coff[s] = n < d.N ? imap(d.bn, n) : -1;
     }
     const bool use_beta = d.beta.x != 0.0 || d.beta.y != 0.0;
+    const int aq16 = TK / d.ak.d2, ar16 = TK % d.ak.d2, bq16 = TK / d.bk.d2, br16 = TK % d.bk.d2;
     for (int bz = blockIdx.z; bz < d.batch * ksplit; bz += gridDim.z) {
         const int b = bz / ksplit, ks = bz % ksplit;
         const int rchunk = d.nred > 1 ? (d.nred + ksplit - 1) / ksplit : 1;
@@ -67,13 +88,21 @@ __global__ void __launch_bounds__(256) tgemm_kernel(TGemm d, const TA *__restric
         for (int r = rbeg; r < rend; ++r) {
             const TA *Ab = A + d.offA[(i64)b * d.nred + r];
             const T *Bb = B + d.offB[(i64)b * d.nred + r];
+            KPos ap[4], bp[4];
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                ap[s] = kpos(d.ak, kbeg + a_kk[s]);
+                bp[s] = kpos(d.bk, kbeg + b_kk[s]);
+            }
             for (int k0 = kbeg; k0 < kend; k0 += TK) {
 #pragma unroll
                 for (int s = 0; s < 4; ++s) {
                     const int k = k0 + a_kk[s];
-                    As[a_kk[s]][a_row[s]] = (a_roff[s] >= 0 && k < kend) ? cvt2(Ab[a_roff[s] + imap(d.ak, k)], T()) : zero2<T>();
+                    As[a_kk[s]][a_row[s]] = (a_roff[s] >= 0 && k < kend) ? cvt2(Ab[a_roff[s] + koff(d.ak, ap[s])], T()) : zero2<T>();
                     const int kb = k0 + b_kk[s];
-                    Bs[b_kk[s]][b_col[s]] = (b_coff[s] >= 0 && kb < kend) ? Bb[imap(d.bk, kb) + b_coff[s]] : zero2<T>();
+                    Bs[b_kk[s]][b_col[s]] = (b_coff[s] >= 0 && kb < kend) ? Bb[koff(d.bk, bp[s]) + b_coff[s]] : zero2<T>();
+                    kadvance(d.ak, aq16, ar16, ap[s]);
+                    kadvance(d.bk, bq16, br16, bp[s]);
                 }
                 __syncthreads();
 #pragma unroll
