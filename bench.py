@@ -46,7 +46,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 TF32_NOMINAL_RATIO = 1.1 / 2.25
 
 
-KERNEL_NAMES = {100: "tc_zgemm_tma_kernel", 101: "tc_zgemm_kernel", 102: "tc_zgemm_bulk_kernel", 200: "zgemm_smallm_kernel",
+KERNEL_NAMES = {100: "tc_zgemm_tma_kernel", 101: "tc_zgemm_kernel", 102: "tc_zgemm_bulk_kernel", 103: "tc_zgemm_oz_kernel",
+                200: "zgemm_smallm_kernel",
                 300: "tc_zgemm_kernel<FP64-stored A>", 301: "tgemm_kernel<float, FP64-stored A>", 400: "tgemm_kernel"}
 # the SIMT launcher's tile candidates in its order: per-thread rows, columns of complex outputs,
 # thread rows of the CTA
@@ -91,6 +92,8 @@ def parse():
     ap.add_argument("--no-chosen", action="store_true", help="skip the chosen-form measurement")
     ap.add_argument("--chosen-prec", default="tf32x3", choices=["tf32x3", "fp32"],
                     help="inner sigma of the chosen form: tensor cores (3xTF32) or FP32 SIMT")
+    ap.add_argument("--refine", default="fp64", choices=["fp64", "fp64_tc"],
+                    help="true residual of the chosen form: FP64 SIMT sigma, or the FP64-accurate sliced tensor-core sigma")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -254,7 +257,8 @@ def gpu_arm(args):
     Gd = torch.zeros((nk, 1, N, N), dtype=torch.complex128, device=dev)
 
     def options(prec, K=-1, orbitals=None):
-        kw = dict(prec=prec, tol=TOL, restart_m=40, max_iter=4000, max_refine=40, kpoint=K)
+        kw = dict(prec=prec, tol=TOL, restart_m=40, max_iter=4000, max_refine=40, kpoint=K,
+                  refine_prec=B.FP64_TC if args.refine == "fp64_tc" else B.FP64)
         if orbitals is not None:
             kw.update(orbital_first=orbitals[0], orbital_count=orbitals[1])
         return B.default_options(**kw)

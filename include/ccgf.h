@@ -59,7 +59,17 @@ typedef enum {
                             in FP32, inside FP64 refinement; contractions too small for a 128-row
                             tile run as in CCGF_FP32. A tensor-core wait that runs past its limit
                             (ccgf_options::device_wait_timeout_ms) makes the call return
-                            CCGF_ERR_TIMEOUT. */
+                            CCGF_ERR_TIMEOUT. */,
+    CCGF_FP64_TC = 3     /* FP64-accurate sigma on the tensor cores: each FP64 operand of a contraction
+                            whose A block is a stored intermediate is cut into integer slices of 8
+                            bits under a per-row (per-column) power of two; their products and
+                            sums of up to 256 of them are exact in tcgen05.mma.kind::tf32, so every
+                            product term above 2^-40 of the leading one is formed exactly and the
+                            rest in FP32 (error ~1e-12 of sum |a||b|). Partial sums are drained into
+                            double-word FP32 accumulators and the result written in FP64. The other
+                            contractions, and those whose sliced copy does not fit in device memory
+                            (3 x the FP64 intermediate), run in FP64 SIMT. Treated as FP64 by the
+                            solver (no refinement). Waits as in CCGF_TF32X3. */
 } ccgf_precision;
 
 typedef enum { CCGF_SECTOR_IP = 1, CCGF_SECTOR_EA = 2, CCGF_SECTOR_BOTH = 3 } ccgf_sector;
@@ -112,6 +122,8 @@ typedef struct {
                                  (2<am|ef> - <am|fe>) r2 term of the EA singles and the T2 part of
                                  the EA ladder are then formed in each sigma from the
                                  density-fitting factors (same operator, less memory)       */
+    ccgf_precision refine_prec; /* solve with CCGF_FP32 / CCGF_TF32X3: the true residual's sigma,
+                                 CCGF_FP64 (default) or CCGF_FP64_TC                        */
 } ccgf_options;
 
 typedef struct {

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libccgf.so")
 
 CCGF_OK, CCGF_NOT_CONVERGED = 0, 1
 CCGF_ERR_INVALID_ARG, CCGF_ERR_OOM, CCGF_ERR_CUDA, CCGF_ERR_NAN, CCGF_ERR_TIMEOUT = -1, -2, -3, -4, -5
-FP64, FP32, TF32X3 = 0, 1, 2
+FP64, FP32, TF32X3, FP64_TC = 0, 1, 2, 3
 IP, EA, BOTH = 1, 2, 3
 
 
@@ -31,7 +31,7 @@ class Options(C.Structure):
     _fields_ = [("prec", C.c_int), ("tol", C.c_double), ("restart_m", C.c_int), ("max_iter", C.c_int),
                 ("max_refine", C.c_int), ("omega_chunk", C.c_int), ("device_wait_timeout_ms", C.c_double),
                 ("warm_start", C.c_int), ("kpoint", C.c_int), ("orbital_first", C.c_int), ("orbital_count", C.c_int),
-                ("direct_terms", C.c_int)]
+                ("direct_terms", C.c_int), ("refine_prec", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -48,6 +48,7 @@ void destroy(ccgf_handle *h) {
     dfree(h->abi_x);
     dfree(h->abi_y);
     tc_free(h);
+    oz_free(h);
     delete h;
 }
 
@@ -69,6 +70,7 @@ void ccgf_default_options(ccgf_options *opt) {
     opt->orbital_first = 0;
     opt->orbital_count = 0;
     opt->direct_terms = 0;
+    opt->refine_prec = CCGF_FP64;
 }
 
 const char *ccgf_status_string(ccgf_status s) {
@@ -150,12 +152,16 @@ ccgf_status ccgf_dims(const ccgf_handle *h, int *nk, int *nocc, int *nvir, long 
     return CCGF_OK;
 }
 
+static bool valid_prec(ccgf_precision p) {
+    return p == CCGF_FP64 || p == CCGF_FP32 || p == CCGF_TF32X3 || p == CCGF_FP64_TC;
+}
+
 static ccgf_status sigma_abi(ccgf_handle *h, int sector, int kshift, long long nvec, const double *x, double *y,
                              ccgf_precision prec, void *stream) {
     if (!h || !x || !y) { set_last_error("NULL handle or vector"); return CCGF_ERR_INVALID_ARG; }
     if (kshift < 0 || kshift >= h->nk) { set_last_error("kshift out of range"); return CCGF_ERR_INVALID_ARG; }
     if (nvec < 1 || nvec > 65536) { set_last_error("nvec must be in [1, 65536]"); return CCGF_ERR_INVALID_ARG; }
-    if (prec != CCGF_FP64 && prec != CCGF_FP32 && prec != CCGF_TF32X3) { set_last_error("unknown precision"); return CCGF_ERR_INVALID_ARG; }
+    if (!valid_prec(prec)) { set_last_error("unknown precision"); return CCGF_ERR_INVALID_ARG; }
     cudaStream_t st = (cudaStream_t)stream;
     const i64 D = sector == CCGF_SECTOR_IP ? h->dim_ip : h->dim_ea;
     const int nv = (int)nvec;
@@ -169,7 +175,7 @@ static ccgf_status sigma_abi(ccgf_handle *h, int sector, int kshift, long long n
     launch_transpose_out(h->abi_y.p, (double2 *)y, D, nv, nv, st);
     h->launches += 2;
     CCGF_CUDA_TRY(cudaGetLastError());
-    if (prec == CCGF_TF32X3) return tc_error_check(h, st);
+    if (prec == CCGF_TF32X3 || prec == CCGF_FP64_TC) return tc_error_check(h, st);
     return CCGF_OK;
 }
 
@@ -207,7 +213,7 @@ ccgf_status ccgf_solve_gf(ccgf_handle *h, int sectors, int nomega, const double 
         set_last_error("invalid options (tol > 0, restart_m >= 2, max_iter >= 1, max_refine >= 1, omega_chunk >= 1)");
         return CCGF_ERR_INVALID_ARG;
     }
-    if (o.prec != CCGF_FP64 && o.prec != CCGF_FP32 && o.prec != CCGF_TF32X3) { set_last_error("unknown precision"); return CCGF_ERR_INVALID_ARG; }
+    if (!valid_prec(o.prec) || (o.refine_prec != CCGF_FP64 && o.refine_prec != CCGF_FP64_TC)) { set_last_error("unknown precision"); return CCGF_ERR_INVALID_ARG; }
     if (!valid_wait(o.device_wait_timeout_ms)) { set_last_error("device_wait_timeout_ms must be in (0, 60000]"); return CCGF_ERR_INVALID_ARG; }
     if (o.kpoint < -1 || o.kpoint >= h->nk || o.orbital_first < 0 || o.orbital_count < 0 ||
         o.orbital_first + o.orbital_count > h->n || (o.orbital_count == 0 && o.orbital_first != 0)) {
@@ -244,7 +250,7 @@ ccgf_status ccgf_solve_gf_mor(ccgf_handle *h, int sectors, int n_mor, const doub
         set_last_error("invalid options");
         return CCGF_ERR_INVALID_ARG;
     }
-    if (o.prec != CCGF_FP64 && o.prec != CCGF_FP32 && o.prec != CCGF_TF32X3) { set_last_error("unknown precision"); return CCGF_ERR_INVALID_ARG; }
+    if (!valid_prec(o.prec) || (o.refine_prec != CCGF_FP64 && o.refine_prec != CCGF_FP64_TC)) { set_last_error("unknown precision"); return CCGF_ERR_INVALID_ARG; }
     struct WaitScope {
         ccgf_handle *h;
         unsigned long long saved;
@@ -315,7 +321,7 @@ ccgf_status ccgf_tensor_wait_selftest(double limit_ms, void *stream) {
     return CCGF_OK;
 }
 int ccgf_sigma_step_kernel(const ccgf_handle *h, int sector, int kshift, int step, ccgf_precision prec) {
-    if (!h || (int)prec < 0 || (int)prec > 2) return -1;
+    if (!h || !valid_prec(prec)) return -1;
     return plan_step_choice(h, sector, kshift, step, (int)prec);
 }
 

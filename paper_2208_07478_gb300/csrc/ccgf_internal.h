@@ -207,7 +207,7 @@ struct SigmaStep {
     i64 rowA_pos;                       // GEMM: position of offA / rsA per (batch, reduction), -1 if not integral
     i64 bslot_pos, bsrc_pos;            // GEMM: slot of each (batch, reduction) B block, offsets of the distinct blocks
     int nslots;                         // number of distinct B blocks
-    int choice[3];                      // GEMM kernel measured per precision (0 = not tuned; see sigma.cu)
+    int choice[4];                      // GEMM kernel measured per precision index (0 = not tuned; see sigma.cu)
 };
 struct SigmaPlan {
     int sector, K, nv;
@@ -261,6 +261,10 @@ struct ccgf_handle {
     // error flag of the tensor-core GEMMs and their TF32-split operands (made on first CCGF_TF32X3 use)
     DBuf<int> tc_err;
     void *tc_ops = nullptr;
+    // FP64-accurate tensor-core path (tc_gemm.cu): sliced planes of the intermediates, made on first use
+    // only while oz_reserve bytes of device memory stay free
+    void *oz_ops = nullptr;
+    size_t oz_reserve = (size_t)4 << 30;
     // cached plans, index (sector-1)*nk + K, valid for plan_nv columns
     std::vector<SigmaPlan *> plans;
     int plan_nv = 0;
@@ -305,6 +309,12 @@ void launch_wait_selftest(double limit_ms, int *err, cudaStream_t st);
 // tc_gemm.cu: TF32 hi / lo copies of every FP32 intermediate, freed by tc_free
 // (only for blocks with an FP32 copy, and only while `reserve` bytes of device memory stay free)
 ccgf_status tc_prepare(ccgf_handle *h, cudaStream_t st, size_t reserve);
+// FP64-accurate complex GEMM on the tensor cores (sliced operands; C and B FP64, A a stored intermediate
+// with TMA-addressable rows): returns launches, 0 when the shape, the tables or device memory do not allow it
+bool tc_zgemm_oz_supported(const GemmDesc &d);
+int launch_tc_zgemm_oz(ccgf_handle *h, int a_buf, const GemmDesc &d, const i64 *rowA, const i64 *bslot, const i64 *bsrc, int nslots,
+                       const double2 *B, double2 *C, int *err, cudaStream_t st);
+void oz_free(ccgf_handle *h);
 // sigma.cu: FP32 copies of the intermediates (large blocks only while `reserve` bytes stay free)
 ccgf_status ensure_fp32(ccgf_handle *h, cudaStream_t st, size_t reserve);
 void tc_free(ccgf_handle *h);

@@ -906,7 +906,7 @@ inline unsigned gsz(i64 n) {
 // k in 1..zgemm_tile_count() = SIMT kernel with the launcher's k-th tile, k + 1000 s = the same
 // with K split over s CTAs (s >= 2, partial sums reduced by a second kernel), the few-row kernel
 // (200), or one of the three tensor-core kernels (100-102)
-enum { CHOICE_TC_TMA = 100, CHOICE_TC_REG = 101, CHOICE_TC_BULK = 102, CHOICE_SMALLM = 200, CHOICE_SPLIT = 1000 };
+enum { CHOICE_TC_TMA = 100, CHOICE_TC_REG = 101, CHOICE_TC_BULK = 102, CHOICE_TC_OZ = 103, CHOICE_SMALLM = 200, CHOICE_SPLIT = 1000 };
 
 // one GEMM step with the given choice; returns the number of launches (0: choice not applicable)
 template <typename R>
@@ -928,6 +928,16 @@ int run_gemm_step(ccgf_handle *h, const SigmaPlan *P, const SigmaStep &s, int ch
             if (tensor_cores && tc_zgemm_supported(d)) return launch_tc_zgemm_a64(d, h->W[s.a_buf].p, scr, C, h->tc_err.p, st);
             return launch_tgemm_a64(tgemm_of(d), h->W[s.a_buf].p, scr, C, st, scr + P->seg[SEG_SPLITK],
                                     P->seg[SEG_END] - P->seg[SEG_SPLITK]);
+        }
+    }
+    if constexpr (sizeof(R) == 8) {
+        // CCGF_FP64_TC: the FP64-accurate sliced tensor-core GEMM where the step allows it (the default)
+        if (tensor_cores && (choice == 0 || choice == CHOICE_TC_OZ)) {
+            int n = 0;
+            if (s.rowA_pos >= 0)
+                n = launch_tc_zgemm_oz(h, s.a_buf, d, offs + s.rowA_pos, offs + s.bslot_pos, offs + s.bsrc_pos, s.nslots, scr, C,
+                                       h->tc_err.p, st);
+            if (n > 0 || choice == CHOICE_TC_OZ) return n;
         }
     }
     if (choice == CHOICE_SMALLM) return launch_zgemm_smallm<R>(d, A, scr, C, st);
@@ -1041,6 +1051,7 @@ ccgf_status autotune_plan(ccgf_handle *h, SigmaPlan *P, int pi, bool tensor_core
         // a contraction whose runs are long is tuned only until 1.5 s of timing has been spent
         std::vector<int> cand;
         const bool tc_ok = sizeof(R) == 4 && tensor_cores && tc_zgemm_supported(g);
+        if (sizeof(R) == 8 && tensor_cores && s.rowA_pos >= 0 && tc_zgemm_oz_supported(g)) cand.push_back(CHOICE_TC_OZ);
         if (tc_ok) {
             if (s.rowA_pos >= 0) {
                 cand.push_back(CHOICE_TC_BULK);
@@ -1104,7 +1115,7 @@ void run_plan(ccgf_handle *h, SigmaPlan *P, const double2 *x, double2 *y, cudaSt
               bool tensor_cores = false) {
     typedef typename cvec<R>::T T;
     const bool f64 = sizeof(R) == 8;
-    const int pi = f64 ? 0 : (tensor_cores ? 2 : 1);
+    const int pi = f64 ? (tensor_cores ? 3 : 0) : (tensor_cores ? 2 : 1);
     T *scr = arena ? arena : (f64 ? (T *)h->scratch.p : (T *)h->scratch_f.p);
     const i64 D = P->sector == CCGF_SECTOR_IP ? h->dim_ip : h->dim_ea;
     const i64 n = D * P->nv;
@@ -1271,7 +1282,7 @@ const char *plan_step_name(const ccgf_handle *h, int sector, int K, int step) {
 void set_autotune(bool on) { g_autotune.store(on ? 1 : 0); }
 int plan_step_choice(const ccgf_handle *h, int sector, int K, int step, int pi) {
     const SigmaPlan *P = plan_of(h, sector, K);
-    if (!P || step < 0 || step >= (int)P->steps.size() || pi < 0 || pi > 2) return -1;
+    if (!P || step < 0 || step >= (int)P->steps.size() || pi < 0 || pi > 3) return -1;
     const SigmaStep &s = P->steps[step];
     if (s.kind == STEP_TGEMM) return 400;
     if (s.kind != STEP_GEMM) return -1;
@@ -1284,10 +1295,12 @@ int plan_step_choice(const ccgf_handle *h, int sector, int K, int step, int pi) 
 }
 
 // Drops what the handle keeps only for speed and rebuilds on demand: the FP32 copies of the
-// intermediates (ensure_fp32), their TF32 hi / lo splits (tc_prepare), the sigma scratch arenas, the
-// split-K workspaces and the ABI transposes. Synchronises the device (cudaFree).
+// intermediates (ensure_fp32), their TF32 hi / lo splits (tc_prepare), the sliced planes of the
+// FP64-accurate tensor-core path, the sigma scratch arenas and the split-K workspaces.
+// Synchronises the device (cudaFree).
 void release_caches(ccgf_handle *h) {
     tc_free(h);
+    oz_free(h);
     for (int b = 0; b < NBUF; ++b) dfree(h->Wf[b]);
     h->fp32_done = false;
     dfree(h->scratch);
@@ -1295,8 +1308,7 @@ void release_caches(ccgf_handle *h) {
     dfree(h->yf);
     dfree(h->splitw64);
     dfree(h->splitw32);
-    dfree(h->abi_x);
-    dfree(h->abi_y);
+    // not the ABI transposes: a sigma call that releases the caches is reading and writing them
 }
 
 void free_plans(ccgf_handle *h) {
@@ -1359,7 +1371,12 @@ ccgf_status sigma_apply(ccgf_handle *h, int sector, int K, int nv, const double2
         P = np;
     }
     const i64 D = sector == CCGF_SECTOR_IP ? h->dim_ip : h->dim_ea;
-    if (prec == CCGF_FP64) {
+    if (prec == CCGF_FP64 || prec == CCGF_FP64_TC) {
+        const bool tc = prec == CCGF_FP64_TC;
+        if (tc && !h->tc_err.p) {
+            CCGF_TRY(dalloc(h->tc_err, 1));
+            CCGF_CUDA_TRY(cudaMemset(h->tc_err.p, 0, sizeof(int)));
+        }
         if (h->scratch.n < P->scratch_elems) {
             CCGF_CUDA_TRY(cudaStreamSynchronize(st));
             dfree(h->scratch);
@@ -1369,8 +1386,8 @@ ccgf_status sigma_apply(ccgf_handle *h, int sector, int K, int nv, const double2
                 CCGF_TRY(dalloc(h->scratch, P->scratch_elems));
             }
         }
-        if (autotune_enabled()) CCGF_TRY(autotune_plan<double>(h, P, 0, false, (double2 *)h->scratch.p, y, st));
-        run_plan<double>(h, P, x, y, st);
+        if (autotune_enabled()) CCGF_TRY(autotune_plan<double>(h, P, tc ? 3 : 0, tc, (double2 *)h->scratch.p, y, st));
+        run_plan<double>(h, P, x, y, st, nullptr, tc);
     } else {
         if (h->scratch_f.n < P->scratch_elems || h->yf.n < D * nv) {
             CCGF_CUDA_TRY(cudaStreamSynchronize(st));

@@ -543,7 +543,10 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
     // then the frequency chunk shrinks. Low-precision copies of the intermediates are decided first,
     // leaving room for the smallest batch the largest sector needs.
     const i64 Dmax_s = (sectors & CCGF_SECTOR_EA) ? h->dim_ea : h->dim_ip;
-    const bool lowp = opt->prec != CCGF_FP64;
+    // low-precision inner sigma (iterative refinement); CCGF_FP64_TC counts as FP64
+    const bool lowp = opt->prec == CCGF_FP32 || opt->prec == CCGF_TF32X3;
+    // sigma of the true residual
+    const ccgf_precision rprec = opt->prec == CCGF_FP64_TC ? CCGF_FP64_TC : (lowp ? opt->refine_prec : CCGF_FP64);
     auto column_bytes = [&](i64 D, int mm) -> double {
         const double scratch = (double)sigma_scratch_per_column(h) * (16.0 + (lowp ? 8.0 : 0.0)) + (lowp ? 8.0 * D : 0.0);
         return 16.0 * D * (mm + 7) + scratch + 16.0 * 304 * N;
@@ -683,7 +686,7 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                     if (used) {
                         auto resid2 = [&](const double2 *x, double2 *r, std::vector<double> &out) -> ccgf_status {
                             CCGF_TRY(sigma_apply(h, sector, K, nv, x, AU.p, opt->prec, st));
-                            if (opt->prec == CCGF_FP64) S.fp64_sigma_calls++; else S.lowp_sigma_calls++;
+                            if (!lowp) S.fp64_sigma_calls++; else S.lowp_sigma_calls++;
                             residual_kernel<<<rg.blocks, rg.threads, 0, st>>>(Sh, B.p, x, AU.p, r, D, nv, rg.cw, rg.ry);
                             h->launches++;
                             CCGF_CUDA_TRY(cudaMemsetAsync(beta2.p, 0, sizeof(double) * nv, st));
@@ -733,7 +736,7 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                 std::vector<double> tg_inner(nv);
                 auto true_residual = [&]() -> ccgf_status {
                     cudaEventRecord(er0, st);
-                    CCGF_TRY(sigma_apply(h, sector, K, nv, X.p, AU.p, CCGF_FP64, st));
+                    CCGF_TRY(sigma_apply(h, sector, K, nv, X.p, AU.p, rprec, st));
                     cudaEventRecord(er1, st);
                     refine_pending = true;
                     S.fp64_sigma_calls++;
@@ -795,7 +798,7 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
                         cudaEventRecord(es0, st);
                         CCGF_TRY(sigma_apply(h, sector, K, nv, U.p, AU.p, opt->prec, st));
                         cudaEventRecord(es1, st);
-                        if (opt->prec == CCGF_FP64) S.fp64_sigma_calls++; else S.lowp_sigma_calls++;
+                        if (!lowp) S.fp64_sigma_calls++; else S.lowp_sigma_calls++;
                         shift_kernel<<<rg.blocks, rg.threads, 0, st>>>(Sh, U.p, AU.p, Vn, D, nv, rg.cw, rg.ry);
                         h->launches++;
                         for (int pass = 0; pass < 2; ++pass) {
@@ -925,6 +928,6 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
     S.kernel_launches = h->launches - launches0;
     if (stats) *stats = S;
     dfree(Gd);
-    if (opt->prec == CCGF_TF32X3) CCGF_TRY(tc_error_check(h, st));
+    if (opt->prec == CCGF_TF32X3 || rprec == CCGF_FP64_TC) CCGF_TRY(tc_error_check(h, st));
     return final_status;
 }

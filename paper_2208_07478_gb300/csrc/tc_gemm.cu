@@ -1073,3 +1073,517 @@ int launch_tc_zgemm_bulk(ccgf_handle *h, int a_buf, const GemmDesc &d, const i64
 void launch_wait_selftest(double limit_ms, int *err, cudaStream_t st) {
     wait_selftest_kernel<<<1, 32, 0, st>>>((unsigned long long)(limit_ms * 1e6), err);
 }
+
+// ----------------------------------------------------------------------------- FP64-accurate variant
+// Complex FP64 GEMM on the tensor cores by exact slicing (after Ozaki et al., error-free
+// transformation of matrix products by splitting each operand into slices whose products are
+// exact): every FP64 value x of a row of A (column of B) with max |x| < 2^e is written as
+//   x = 2^e * (s0 2^-8 + s1 2^-16 + s2 2^-24 + s3 2^-32 + s4 2^-40) + r,   |r| <= 2^(e-41),
+// with integers |s0| <= 256, |si| <= 128. Integers of this size are exact in TF32, their products
+// are exact, and a sum of up to 256 of them (< 2^24) is exact in the FP32 accumulator of
+// tcgen05.mma.kind::tf32. Per output x*y = 2^(eA+eB) (s0 t0 2^-16 + (s0 t1 + s1 t0) 2^-24 + T 2^-16),
+// where T = sum over 2 <= i + j <= 4 of (si 2^-8i)(tj 2^-8j) holds the terms below 2^-16 of the
+// leading one, so the rounding of its FP32 accumulation stays near 2^-40 of the result; terms with
+// i + j > 4 are dropped (< 2^-40). Per 8 real K the CTA issues 15 MMAs into three TMEM accumulators
+// (T0 = s0 t0, T1 = s0 t1 + s1 t0, T), double-buffered; every chunk of at most 256 real K within one
+// reduction block is drained by the epilogue warps into FP32 double-word accumulators (exact
+// two-sums) scaled by 2^(eA + eB), so the exactness bound of T0 / T1 is never exceeded. Operands:
+// A as six stored planes (s0, s1, s1 2^-8, s2 2^-16, s3 2^-24, s4 2^-32) of the FP64 intermediate
+// with one exponent per stored row, by TMA; B as the same six planes of the 2x2-embedded B' tile
+// with one exponent per (block, column), written by oz_bimage_kernel and fetched by one
+// cp.async.bulk per stage. Result error ~1e-12 of sum |a||b|.
+namespace {
+
+constexpr int OZ_PLANES = 6;
+constexpr int OZ_CHUNK_STAGES = 16;        // 16 stages x 16 real K = 256: the exactness bound of T0 / T1
+constexpr int OZ_MAX_STAGES = 3;
+
+// exponent e with |x| < 2^e for every |x| <= amax (0 when amax = 0)
+__device__ __forceinline__ int oz_exponent(double amax) {
+    int e = 0;
+    if (amax > 0.0) frexp(amax, &e);
+    return e;
+}
+// the six plane values of x (|x| < 2^e)
+__device__ __forceinline__ void oz_slice(double x, int e, float (&p)[OZ_PLANES]) {
+    double t = ldexp(x, 8 - e);   // |t| < 256
+    const double s0 = rint(t);
+    t = (t - s0) * 256.0;
+    const double s1 = rint(t);
+    t = (t - s1) * 256.0;
+    const double s2 = rint(t);
+    t = (t - s2) * 256.0;
+    const double s3 = rint(t);
+    t = (t - s3) * 256.0;
+    const double s4 = rint(t);
+    p[0] = (float)s0;
+    p[1] = (float)s1;
+    p[2] = (float)(s1 * 0x1p-8);
+    p[3] = (float)(s2 * 0x1p-16);
+    p[4] = (float)(s3 * 0x1p-24);
+    p[5] = (float)(s4 * 0x1p-32);
+}
+// 2^e as a double for |e| < 1000
+__device__ __forceinline__ double oz_pow2(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
+
+// planes of an FP64 buffer viewed as rows of rs complex: one block per row (grid-strided)
+__global__ void oz_plane_kernel(const double2 *__restrict__ W, i64 rows, i64 rs, float2 *__restrict__ planes, i64 plane_stride,
+                                int *__restrict__ rowexp) {
+    __shared__ double red[256];
+    for (i64 y = blockIdx.x; y < rows; y += gridDim.x) {
+        const double2 *row = W + y * rs;
+        double m = 0.0;
+        for (i64 k = threadIdx.x; k < rs; k += blockDim.x) m = fmax(m, fmax(fabs(row[k].x), fabs(row[k].y)));
+        red[threadIdx.x] = m;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if ((int)threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+            __syncthreads();
+        }
+        const int e = oz_exponent(red[0]);
+        __syncthreads();
+        if (threadIdx.x == 0) rowexp[y] = e;
+        for (i64 k = threadIdx.x; k < rs; k += blockDim.x) {
+            float pr[OZ_PLANES], pi[OZ_PLANES];
+            oz_slice(row[k].x, e, pr);
+            oz_slice(row[k].y, e, pi);
+#pragma unroll
+            for (int q = 0; q < OZ_PLANES; ++q) planes[q * plane_stride + y * rs + k] = make_float2(pr[q], pi[q]);
+        }
+    }
+}
+
+// exponent of every (slot, column) of B over its K complex entries: one warp per (slot, column)
+__global__ void oz_colexp_kernel(GemmDesc d, const double2 *__restrict__ B, const i64 *__restrict__ bsrc, int nslots,
+                                 int *__restrict__ colexp) {
+    const int lane = threadIdx.x & 31;
+    const i64 nw = (i64)nslots * d.N;
+    for (i64 w = ((i64)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw; w += ((i64)gridDim.x * blockDim.x) >> 5) {
+        const int slot = (int)(w / d.N), n = (int)(w % d.N);
+        const double2 *col = B + bsrc[slot] + (i64)n * d.csB;
+        double m = 0.0;
+        for (int k = lane; k < d.K; k += 32) {
+            const double2 v = col[(i64)k * d.rsB];
+            m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+        if (lane == 0) colexp[w] = oz_exponent(m);
+    }
+}
+
+// B' planes of the slots: per (slot, N tile, K tile) six planes of NR rows x 16 real K in the
+// canonical no-swizzle K-major layout (as bimage_kernel); thread = (slot, N tile, K tile, 4-column
+// group t, k pair kp, column nl)
+__global__ void oz_bimage_kernel(GemmDesc d, const double2 *__restrict__ B, const i64 *__restrict__ bsrc, const int *__restrict__ colexp,
+                                 int nslots, int BNc, int ntiles, int ktiles, float *__restrict__ img) {
+    const int NR = 2 * BNc;
+    const i64 plane = (i64)NR * (2 * BKC3);
+    const i64 chunk = OZ_PLANES * plane;
+    const i64 per_tile = (i64)(BNc / 4) * 16;
+    const i64 total = (i64)nslots * ntiles * ktiles * per_tile;
+    for (i64 i = (i64)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (i64)gridDim.x * blockDim.x) {
+        const int nl = (int)(i & 3), kp = (int)((i >> 2) & 3);
+        i64 r = i >> 4;
+        const int t = (int)(r % (BNc / 4));
+        r /= (BNc / 4);
+        const int kt = (int)(r % ktiles);
+        r /= ktiles;
+        const int nt = (int)(r % ntiles);
+        const int slot = (int)(r / ntiles);
+        const int n = nt * BNc + t * 4 + nl, k = kt * BKC3 + kp * 2;
+        double2 v0 = make_double2(0.0, 0.0), v1 = v0;
+        int e = 0;
+        if (n < d.N) {
+            const double2 *col = B + bsrc[slot] + (i64)n * d.csB;
+            if (k < d.K) v0 = col[(i64)k * d.rsB];
+            if (k + 1 < d.K) v1 = col[(i64)(k + 1) * d.rsB];
+            e = colexp[(i64)slot * d.N + n];
+        }
+        float r0[OZ_PLANES], i0[OZ_PLANES], r1[OZ_PLANES], i1[OZ_PLANES];
+        oz_slice(v0.x, e, r0);
+        oz_slice(v0.y, e, i0);
+        oz_slice(v1.x, e, r1);
+        oz_slice(v1.y, e, i1);
+        float *base = img + (((i64)slot * ntiles + nt) * ktiles + kt) * chunk;
+        const int o_re = t * 128 + kp * 32 + nl * 8, o_im = o_re + 4;   // in floats: row 2n, row 2n+1
+#pragma unroll
+        for (int q = 0; q < OZ_PLANES; ++q) {
+            float *p = base + q * plane;
+            *(float4 *)(p + o_re) = make_float4(r0[q], -i0[q], r1[q], -i1[q]);
+            *(float4 *)(p + o_im) = make_float4(i0[q], r0[q], i1[q], r1[q]);
+        }
+    }
+}
+
+// exact sum of two floats: s + e = a + b
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// (hi, lo) += (vh, vl) in double-word FP32 arithmetic
+__device__ __forceinline__ void dw_add(float &hi, float &lo, float vh, float vl) {
+    float s, e;
+    two_sum(hi, vh, s, e);
+    e = __fadd_rn(e, __fadd_rn(lo, vl));
+    hi = __fadd_rn(s, e);
+    lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+
+}  // namespace
+
+namespace {
+
+// FP64-accurate complex GEMM (see above). NR = 2 BNc real columns (32 or 64); TMEM holds
+// T0 / T1 / T of two chunk buffers at columns q * NR, q = 3 * buffer + accumulator.
+template <int NR>
+__global__ void __launch_bounds__(TMA_THREADS, 1)
+    tc_zgemm_oz_kernel(GemmDesc d, const __grid_constant__ CUtensorMap m0_, const __grid_constant__ CUtensorMap m1_,
+                       const __grid_constant__ CUtensorMap m2_, const __grid_constant__ CUtensorMap m3_,
+                       const __grid_constant__ CUtensorMap m4_, const __grid_constant__ CUtensorMap m5_,
+                       const i64 *__restrict__ rowA, const int *__restrict__ rowexp, i64 arows, const i64 *__restrict__ bslot,
+                       const float *__restrict__ img, const int *__restrict__ colexp, double2 *__restrict__ C, int S, int *err) {
+    constexpr int BNc = NR / 2;
+    constexpr uint32_t NCOLS = NR <= 32 ? 256 : 512;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+    constexpr uint32_t a_bytes = BM * 2 * BKC3 * 4;                      // 8 KB per plane
+    constexpr uint32_t b_plane = (uint32_t)NR * 2 * BKC3 * 4;            // NR x 16 floats
+    constexpr uint32_t b_bytes = OZ_PLANES * b_plane;
+    constexpr uint32_t stage_bytes = OZ_PLANES * a_bytes + b_bytes;
+    uint64_t *full = (uint64_t *)(base + S * stage_bytes);
+    uint64_t *empty = full + OZ_MAX_STAGES;
+    uint64_t *cfull = empty + OZ_MAX_STAGES;   // [2] chunk accumulated
+    uint64_t *cempty = cfull + 2;              // [2] chunk drained
+    uint64_t *accum = cempty + 2;              // every MMA done
+    uint32_t *tmem_slot = (uint32_t *)(accum + 1);
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int b = blockIdx.z, nt = blockIdx.x;
+    const int mb = blockIdx.y * BM, n0 = nt * BNc;
+    const int ktiles = (d.K + BKC3 - 1) / BKC3;
+    const int ntiles = gridDim.x;
+    const int total = d.nred * ktiles;
+    const int cpr = (ktiles + OZ_CHUNK_STAGES - 1) / OZ_CHUNK_STAGES;   // chunks per reduction block
+    const int nchunks = d.nred * cpr;
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int p = 0; p < 2; ++p) {
+            mbar_init(&cfull[p], 1);
+            mbar_init(&cempty[p], 4);
+        }
+        mbar_init(accum, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)), "r"(NCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    volatile int *abort_v = &abort_flag;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            const CUtensorMap *maps[OZ_PLANES] = {&m0_, &m1_, &m2_, &m3_, &m4_, &m5_};
+            int issued = 0;
+            for (int kt = 0; kt < total; ++kt) {
+                const int s = kt % S;
+                if (kt >= S && !mbar_wait_or_abort(&empty[s], ((kt / S) - 1) & 1, abort_v, d.wait_ns)) {
+                    atomicExch(err, 1);
+                    *abort_v = 1;
+                    break;
+                }
+                const int r = kt / ktiles, kk = kt % ktiles;
+                const i64 br = (i64)b * d.nred + r;
+                const int y = (int)rowA[br] + mb;
+                unsigned char *sA = base + s * stage_bytes;
+                const float *src = img + (((i64)bslot[br] * ntiles + nt) * ktiles + kk) * ((i64)b_bytes / 4);
+                mbar_expect_tx(&full[s], stage_bytes);
+#pragma unroll
+                for (int q = 0; q < OZ_PLANES; ++q) tma_load_2d(smem_u32(sA + q * a_bytes), maps[q], 2 * kk * BKC3, y, &full[s]);
+                bulk_load(smem_u32(sA + OZ_PLANES * a_bytes), src, b_bytes, &full[s]);
+                issued = kt + 1;
+            }
+            for (int kt = issued - S > 0 ? issued - S : 0; kt < issued; ++kt)
+                if (!mbar_wait(&full[kt % S], (kt / S) & 1, d.wait_ns)) atomicExch(err, 1);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = make_idesc(NR);
+            // (A plane, B plane, accumulator) of the 15 products
+            const int pa[15] = {0, 0, 1, 0, 0, 0, 2, 2, 2, 3, 3, 3, 4, 4, 5};
+            const int pb[15] = {0, 1, 0, 3, 4, 5, 2, 3, 4, 0, 2, 3, 0, 2, 0};
+            const int pc[15] = {0, 1, 1, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2};
+            int issued = 0, c = -1;
+            for (int kt = 0; kt < total; ++kt) {
+                const int s = kt % S;
+                const int kk = kt % ktiles;
+                const bool cstart = kk % OZ_CHUNK_STAGES == 0;
+                const bool cend = kk % OZ_CHUNK_STAGES == OZ_CHUNK_STAGES - 1 || kk == ktiles - 1;
+                if (cstart) {
+                    ++c;
+                    if (c >= 2 && !mbar_wait_or_abort(&cempty[c & 1], ((c >> 1) - 1) & 1, abort_v, d.wait_ns)) {
+                        atomicExch(err, 1);
+                        *abort_v = 1;
+                        break;
+                    }
+                }
+                if (!mbar_wait_or_abort(&full[s], (kt / S) & 1, abort_v, d.wait_ns)) {
+                    atomicExch(err, 1);
+                    *abort_v = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t sa = smem_u32(base + s * stage_bytes), sb = sa + OZ_PLANES * a_bytes;
+                const uint32_t tacc = tmem + (uint32_t)((c & 1) * 3 * NR);
+#pragma unroll
+                for (int ks = 0; ks < (2 * BKC3) / 8; ++ks) {
+#pragma unroll
+                    for (int q = 0; q < 15; ++q) {
+                        const uint64_t da = make_desc_sw64(sa + pa[q] * a_bytes + ks * 32);
+                        const uint64_t db = make_desc_k16(sb + pb[q] * b_plane + ks * 256);
+                        // the first product into each accumulator of a chunk overwrites it
+                        const bool first = cstart && ks == 0 && (q == 0 || q == 1 || q == 3);
+                        mma_tf32(tacc + (uint32_t)(pc[q] * NR), da, db, idesc, first ? 0u : 1u);
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&empty[s]))
+                             : "memory");
+                if (cend)
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     smem_u32(&cfull[c & 1]))
+                                 : "memory");
+                issued = kt + 1;
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(accum))
+                         : "memory");
+            if (issued < total) *abort_v = 1;
+        }
+    } else {
+        // epilogue: thread = output row (TMEM lane quarter * 32 + lane), NR real columns in double-word FP32
+        const int quarter = warp & 3;
+        const int m = mb + quarter * 32 + lane;
+        float ah[NR], al[NR];
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            ah[j] = 0.f;
+            al[j] = 0.f;
+        }
+        bool ok = true;
+        for (int c = 0; c < nchunks && ok; ++c) {
+            const int r = c / cpr;
+            ok = mbar_wait_or_abort(&cfull[c & 1], (c >> 1) & 1, abort_v, d.wait_ns);
+            if (!__all_sync(0xffffffffu, ok)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const i64 br = (i64)b * d.nred + r;
+            const i64 ya = rowA[br] + m;
+            const int ea = ya < arows ? rowexp[ya] : 0;
+            const int *ce = colexp + (i64)bslot[br] * d.N;
+            const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((c & 1) * 3 * NR);
+#pragma unroll
+            for (int c0 = 0; c0 < NR; c0 += 8) {
+                uint32_t v0[8], v1[8], v2[8];
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                             : "=r"(v0[0]), "=r"(v0[1]), "=r"(v0[2]), "=r"(v0[3]), "=r"(v0[4]), "=r"(v0[5]), "=r"(v0[6]), "=r"(v0[7])
+                             : "r"(tbase + (uint32_t)c0));
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                             : "=r"(v1[0]), "=r"(v1[1]), "=r"(v1[2]), "=r"(v1[3]), "=r"(v1[4]), "=r"(v1[5]), "=r"(v1[6]), "=r"(v1[7])
+                             : "r"(tbase + (uint32_t)(NR + c0)));
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                             : "=r"(v2[0]), "=r"(v2[1]), "=r"(v2[2]), "=r"(v2[3]), "=r"(v2[4]), "=r"(v2[5]), "=r"(v2[6]), "=r"(v2[7])
+                             : "r"(tbase + (uint32_t)(2 * NR + c0)));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int n = n0 + (c0 + j) / 2;
+                    const int eb = n < d.N ? ce[n] : 0;
+                    // value in units of 2^-24: T0 2^8 + T1 + T 2^8 (T0 2^8 + T1 as an exact pair)
+                    float vh, vl;
+                    two_sum(__uint_as_float(v0[j]) * 256.f, __uint_as_float(v1[j]), vh, vl);
+                    vl = __fmaf_rn(__uint_as_float(v2[j]), 256.f, vl);
+                    // scale by 2^(ea + eb - 24): exact inside the FP32 range (below it the term is dropped,
+                    // above it the result becomes infinite, so that no wrong finite value is written)
+                    const int ex = ea + eb - 24 + 127;
+                    const float sc = ex < 1 ? 0.f : (ex > 254 ? __int_as_float(0x7f800000) : __int_as_float(ex << 23));
+                    dw_add(ah[c0 + j], al[c0 + j], vh * sc, vl * sc);
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&cempty[c & 1]);
+        }
+        if (!ok) atomicExch(err, 1);
+        if (__all_sync(0xffffffffu, ok) && !*abort_v && m < d.M) {
+            const double ax = d.alpha.x, ay = d.alpha.y, bx = d.beta.x, by = d.beta.y;
+            const bool use_beta = (bx != 0.0 || by != 0.0);
+            double2 *Cb = C + d.offC[b];
+#pragma unroll
+            for (int q = 0; q < BNc; ++q) {
+                const int n = n0 + q;
+                if (n >= d.N) continue;
+                const double re = (double)ah[2 * q] + (double)al[2 * q], im = (double)ah[2 * q + 1] + (double)al[2 * q + 1];
+                double2 *cp = Cb + (i64)m * d.rsC + (i64)n * d.csC;
+                double2 o;
+                o.x = ax * re - ay * im;
+                o.y = ax * im + ay * re;
+                if (use_beta) {
+                    const double2 cv = *cp;
+                    o.x += bx * cv.x - by * cv.y;
+                    o.y += bx * cv.y + by * cv.x;
+                }
+                *cp = o;
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1) {
+        if (*abort_v) {
+            if (!mbar_wait(accum, 0, d.wait_ns)) atomicExch(err, 1);
+            __syncwarp();
+        }
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
+    }
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------- host side of the FP64-accurate path
+// Six planes and the row exponents of an intermediate, made on first use for one row length
+// (the view its GEMMs use), only while the device keeps its reserve free afterwards.
+struct OzPlanes {
+    i64 rs = 0, rows = 0;
+    DBuf<float2> planes;   // [6][n]
+    DBuf<int> rowexp;      // [rows]
+    CUtensorMap maps[OZ_PLANES];
+};
+struct OzState {
+    OzPlanes *p[NBUF] = {};
+    bool refused[NBUF] = {};
+    DBuf<float> img;
+    DBuf<int> colexp;
+};
+
+static OzState *oz_state(ccgf_handle *h) {
+    if (!h->oz_ops) h->oz_ops = new OzState();
+    return (OzState *)h->oz_ops;
+}
+
+void oz_free(ccgf_handle *h) {
+    OzState *O = (OzState *)h->oz_ops;
+    if (!O) return;
+    for (int b = 0; b < NBUF; ++b) delete O->p[b];
+    delete O;
+    h->oz_ops = nullptr;
+}
+
+static const OzPlanes *oz_planes(ccgf_handle *h, int a_buf, i64 rs, cudaStream_t st) {
+    if (a_buf < BUF_FOO || a_buf >= NBUF || !h->W[a_buf].p || rs <= 0 || (rs & 1)) return nullptr;
+    OzState *O = oz_state(h);
+    if (O->p[a_buf]) return O->p[a_buf]->rs == rs ? O->p[a_buf] : nullptr;
+    if (O->refused[a_buf]) return nullptr;
+    // planes 16-byte aligned: stride rounded up to an even number of complex elements
+    const i64 n = h->W[a_buf].n, rows = n / rs, pstride = (n + 1) & ~(i64)1;
+    EncodeTiledFn enc = encode_fn();
+    size_t fr = 0, tot = 0;
+    const size_t bytes = (size_t)OZ_PLANES * pstride * sizeof(float2) + (size_t)rows * sizeof(int);
+    if (!enc || rows < 1 || rows > (1LL << 31) - 1 || cudaMemGetInfo(&fr, &tot) != cudaSuccess || fr < bytes + h->oz_reserve) {
+        O->refused[a_buf] = true;
+        return nullptr;
+    }
+    OzPlanes *P = new OzPlanes();
+    P->rs = rs;
+    P->rows = rows;
+    if (dalloc(P->planes, OZ_PLANES * pstride) != CCGF_OK || dalloc(P->rowexp, rows) != CCGF_OK) {
+        delete P;
+        O->refused[a_buf] = true;
+        return nullptr;
+    }
+    const unsigned g = (unsigned)std::min<i64>(rows, 152 * 8);
+    oz_plane_kernel<<<g, 256, 0, st>>>(h->W[a_buf].p, rows, rs, P->planes.p, pstride, P->rowexp.p);
+    h->launches++;
+    cuuint64_t dims[2] = {(cuuint64_t)(2 * rs), (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(2 * rs * sizeof(float))};
+    cuuint32_t box[2] = {(cuuint32_t)(2 * BKC3), (cuuint32_t)BM};
+    cuuint32_t estr[2] = {1, 1};
+    for (int q = 0; q < OZ_PLANES; ++q) {
+        CUresult r = enc(&P->maps[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)(P->planes.p + (i64)q * pstride), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            delete P;
+            O->refused[a_buf] = true;
+            return nullptr;
+        }
+    }
+    O->p[a_buf] = P;
+    return P;
+}
+
+template <int NR>
+static void launch_oz_cols(dim3 grid, size_t smem, cudaStream_t st, const GemmDesc &d, const OzPlanes *P, const i64 *rowA,
+                           const i64 *bslot, const float *img, const int *colexp, double2 *C, int S, int *err) {
+    cudaFuncSetAttribute(tc_zgemm_oz_kernel<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    tc_zgemm_oz_kernel<NR><<<grid, TMA_THREADS, smem, st>>>(with_wait_limit(d), P->maps[0], P->maps[1], P->maps[2], P->maps[3],
+                                                           P->maps[4], P->maps[5], rowA, P->rowexp.p, P->rows, bslot, img, colexp, C,
+                                                           S, err);
+}
+
+bool tc_zgemm_oz_supported(const GemmDesc &d) { return d.M > 0 && d.N > 0 && d.K > 0 && d.csA == 1 && (d.rsA % 2) == 0; }
+
+int launch_tc_zgemm_oz(ccgf_handle *h, int a_buf, const GemmDesc &d, const i64 *rowA, const i64 *bslot, const i64 *bsrc, int nslots,
+                       const double2 *B, double2 *C, int *err, cudaStream_t st) {
+    if (!tc_zgemm_oz_supported(d) || !rowA || !bslot || !bsrc || nslots < 1 || !err) return 0;
+    const OzPlanes *P = oz_planes(h, a_buf, d.rsA, st);
+    if (!P) return 0;
+    OzState *O = oz_state(h);
+    const int BNc = d.N <= 16 ? 16 : 32, NR = 2 * BNc;
+    const int ntiles = (int)ceil_div(d.N, BNc), ktiles = (int)ceil_div(d.K, BKC3);
+    const i64 img_floats = (i64)nslots * ntiles * ktiles * OZ_PLANES * NR * (2 * BKC3);
+    const i64 ncol = (i64)nslots * d.N;
+    if (O->img.n < img_floats || O->colexp.n < ncol) {
+        // grow (synchronises: the previous image may still be in use)
+        if (cudaStreamSynchronize(st) != cudaSuccess) return 0;
+        if (O->img.n < img_floats) {
+            dfree(O->img);
+            if (dalloc(O->img, img_floats) != CCGF_OK) return 0;
+        }
+        if (O->colexp.n < ncol) {
+            dfree(O->colexp);
+            if (dalloc(O->colexp, ncol) != CCGF_OK) return 0;
+        }
+    }
+    const size_t stage = (size_t)OZ_PLANES * BM * 2 * BKC3 * 4 + (size_t)OZ_PLANES * NR * 2 * BKC3 * 4;
+    const size_t extra = 1024 + 8 * (2 * OZ_MAX_STAGES + 5) + 16;
+    int S = (int)((227 * 1024 - extra) / stage);
+    if (S > OZ_MAX_STAGES) S = OZ_MAX_STAGES;
+    if (S < 2) return 0;
+    const size_t smem = S * stage + extra;
+    {
+        const i64 g = ceil_div(ncol * 32, 256);
+        oz_colexp_kernel<<<(unsigned)(g > 152 * 16 ? 152 * 16 : g), 256, 0, st>>>(d, B, bsrc, nslots, O->colexp.p);
+        const i64 total = (i64)nslots * ntiles * ktiles * (BNc / 4) * 16;
+        const i64 g2 = ceil_div(total, 256);
+        oz_bimage_kernel<<<(unsigned)(g2 > 152 * 32 ? 152 * 32 : g2), 256, 0, st>>>(d, B, bsrc, O->colexp.p, nslots, BNc, ntiles,
+                                                                                    ktiles, O->img.p);
+    }
+    const dim3 grid((unsigned)ntiles, (unsigned)ceil_div(d.M, BM), (unsigned)d.batch);
+    if (NR == 32)
+        launch_oz_cols<32>(grid, smem, st, d, P, rowA, bslot, O->img.p, O->colexp.p, C, S, err);
+    else
+        launch_oz_cols<64>(grid, smem, st, d, P, rowA, bslot, O->img.p, O->colexp.p, C, S, err);
+    return 3;
+}

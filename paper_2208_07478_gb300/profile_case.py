@@ -28,7 +28,8 @@ def main():
     ap.add_argument("--naux", type=int, default=64)
     ap.add_argument("--nvec", type=int, default=0, help="default: nocc + nvir")
     ap.add_argument("--sector", default="ea", choices=["ip", "ea"])
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "tf32x3"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "tf32x3", "fp64_tc"])
+    ap.add_argument("--refine", default="fp64", choices=["fp64", "fp64_tc"], help="--solve: true-residual sigma")
     ap.add_argument("--calls", type=int, default=1)
     ap.add_argument("--workload", default=None, help="a named synthetic workload (replaces the shape options)")
     ap.add_argument("--solve", action="store_true", help="profile solve_gf instead of one sigma call")
@@ -41,11 +42,12 @@ def main():
     else:
         s = make_system(tuple(a.kmesh), a.nocc, a.nvir, a.naux, seed=1, L_sigma=0.05, t1_sigma=0.01, nomega=0)
     h = B.build_intermediates(s.kmesh, s.nocc, s.nvir, s.naux, s.mo_energy, s.L, s.t1, s.t2)
-    prec = {"fp64": B.FP64, "fp32": B.FP32, "tf32x3": B.TF32X3}[a.prec]
+    prec = {"fp64": B.FP64, "fp32": B.FP32, "tf32x3": B.TF32X3, "fp64_tc": B.FP64_TC}[a.prec]
     if a.solve:
         G = torch.zeros((s.nk, 1, s.nmo, s.nmo), dtype=torch.complex128, device="cuda")
         om = s.omega[[len(s.omega) // 2]] if len(s.omega) else np.zeros(1)
-        opt = B.default_options(prec=prec, tol=1e-6, restart_m=40, max_iter=4000, max_refine=40)
+        opt = B.default_options(prec=prec, tol=1e-6, restart_m=40, max_iter=4000, max_refine=40,
+                                refine_prec=B.FP64_TC if a.refine == "fp64_tc" else B.FP64)
         B.solve_gf(h, B.BOTH, om, s.eta, G, options=opt, on_device=True)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("profiled")
