@@ -63,12 +63,13 @@ typedef enum {
     CCGF_FP64_TC = 3     /* FP64-accurate sigma on the tensor cores: each FP64 operand of a contraction
                             whose A block is a stored intermediate is cut into integer slices of 8
                             bits under a per-row (per-column) power of two; their products and
-                            sums of up to 256 of them are exact in tcgen05.mma.kind::tf32, so every
-                            product term above 2^-40 of the leading one is formed exactly and the
-                            rest in FP32 (error ~1e-12 of sum |a||b|). Partial sums are drained into
-                            double-word FP32 accumulators and the result written in FP64. The other
+                            sums below 2^24 are exact in tcgen05.mma.kind::tf32, so the product
+                            terms down to 2^-32 of the leading one are formed exactly, those down
+                            to 2^-40 with FP32 rounding far below that, and smaller ones dropped
+                            (error ~2^-40 of sum |a||b|). Partial sums are drained into double-word
+                            FP32 accumulators and the result written in FP64. The other
                             contractions, and those whose sliced copy does not fit in device memory
-                            (3 x the FP64 intermediate), run in FP64 SIMT. Treated as FP64 by the
+                            (3.5 x the FP64 intermediate), run in FP64 SIMT. Treated as FP64 by the
                             solver (no refinement). Waits as in CCGF_TF32X3. */
 } ccgf_precision;
 

@@ -1286,7 +1286,7 @@ int plan_step_choice(const ccgf_handle *h, int sector, int K, int step, int pi) 
     const SigmaStep &s = P->steps[step];
     if (s.kind == STEP_TGEMM) return 400;
     if (s.kind != STEP_GEMM) return -1;
-    if (pi > 0 && !h->Wf[s.a_buf].p) {
+    if ((pi == 1 || pi == 2) && !h->Wf[s.a_buf].p) {
         // FP64-stored block (no FP32 copy): register-fed tensor cores or the tensor GEMM, rounding on load
         GemmDesc d = s.g;
         return (pi == 2 && tc_zgemm_supported(d)) ? 300 : 301;

@@ -1079,23 +1079,24 @@ void launch_wait_selftest(double limit_ms, int *err, cudaStream_t st) {
 // transformation of matrix products by splitting each operand into slices whose products are
 // exact): every FP64 value x of a row of A (column of B) with max |x| < 2^e is written as
 //   x = 2^e * (s0 2^-8 + s1 2^-16 + s2 2^-24 + s3 2^-32 + s4 2^-40) + r,   |r| <= 2^(e-41),
-// with integers |s0| <= 256, |si| <= 128. Integers of this size are exact in TF32, their products
-// are exact, and a sum of up to 256 of them (< 2^24) is exact in the FP32 accumulator of
-// tcgen05.mma.kind::tf32. Per output x*y = 2^(eA+eB) (s0 t0 2^-16 + (s0 t1 + s1 t0) 2^-24 + T 2^-16),
-// where T = sum over 2 <= i + j <= 4 of (si 2^-8i)(tj 2^-8j) holds the terms below 2^-16 of the
-// leading one, so the rounding of its FP32 accumulation stays near 2^-40 of the result; terms with
-// i + j > 4 are dropped (< 2^-40). Per 8 real K the CTA issues 15 MMAs into three TMEM accumulators
-// (T0 = s0 t0, T1 = s0 t1 + s1 t0, T), double-buffered; every chunk of at most 256 real K within one
-// reduction block is drained by the epilogue warps into FP32 double-word accumulators (exact
-// two-sums) scaled by 2^(eA + eB), so the exactness bound of T0 / T1 is never exceeded. Operands:
-// A as six stored planes (s0, s1, s1 2^-8, s2 2^-16, s3 2^-24, s4 2^-32) of the FP64 intermediate
-// with one exponent per stored row, by TMA; B as the same six planes of the 2x2-embedded B' tile
-// with one exponent per (block, column), written by oz_bimage_kernel and fetched by one
-// cp.async.bulk per stage. Result error ~1e-12 of sum |a||b|.
+// rounding to nearest at each step, so |s0| <= 256 and |s1..s4| <= 128. Integers of this size are
+// exact in TF32, so are their products, and sums below 2^24 are exact in the FP32 accumulator of
+// tcgen05.mma.kind::tf32. Per output
+//   x*y = 2^(eA+eB) (T0 2^-16 + T1 2^-24 + T2 2^-32 + T 2^-16),
+//   T0 = s0 t0, T1 = s0 t1 + s1 t0, T2 = s0 t2 + s1 t1 + s2 t0 (integers, exact over 128 real K),
+//   T = sum over i + j in {3, 4} of (si 2^-8i)(tj 2^-8j) (below 2^-24 of the leading term, so the FP32
+//   rounding of its accumulation is ~2^-48 of it); terms with i + j > 4 (< 2^-40) are dropped.
+// Per 8 real K the CTA issues 15 MMAs into the four TMEM accumulators of one of two chunk buffers;
+// every chunk of at most 128 real K within one reduction block is drained by the epilogue warps into
+// FP32 double-word accumulators scaled by 2^(eA + eB) while the MMAs fill the other buffer. Operands:
+// A as seven stored planes (s0, s1, s2 and s1 2^-8, s2 2^-16, s3 2^-24, s4 2^-32) of the FP64
+// intermediate with one exponent per stored row, by TMA; B as the same seven planes of the
+// 2x2-embedded B' tile with one exponent per (block, column), written by oz_bimage_kernel and fetched
+// by one cp.async.bulk per stage. Error ~2^-40 of sum |a||b|.
 namespace {
 
-constexpr int OZ_PLANES = 6;
-constexpr int OZ_CHUNK_STAGES = 16;        // 16 stages x 16 real K = 256: the exactness bound of T0 / T1
+constexpr int OZ_PLANES = 7;
+constexpr int OZ_CHUNK_STAGES = 8;         // 8 stages x 16 real K = 128: the exactness bound of T2
 constexpr int OZ_MAX_STAGES = 3;
 
 // exponent e with |x| < 2^e for every |x| <= amax (0 when amax = 0)
@@ -1104,7 +1105,7 @@ __device__ __forceinline__ int oz_exponent(double amax) {
     if (amax > 0.0) frexp(amax, &e);
     return e;
 }
-// the six plane values of x (|x| < 2^e)
+// the seven plane values of x (|x| < 2^e)
 __device__ __forceinline__ void oz_slice(double x, int e, float (&p)[OZ_PLANES]) {
     double t = ldexp(x, 8 - e);   // |t| < 256
     const double s0 = rint(t);
@@ -1118,10 +1119,11 @@ __device__ __forceinline__ void oz_slice(double x, int e, float (&p)[OZ_PLANES])
     const double s4 = rint(t);
     p[0] = (float)s0;
     p[1] = (float)s1;
-    p[2] = (float)(s1 * 0x1p-8);
-    p[3] = (float)(s2 * 0x1p-16);
-    p[4] = (float)(s3 * 0x1p-24);
-    p[5] = (float)(s4 * 0x1p-32);
+    p[2] = (float)s2;
+    p[3] = (float)(s1 * 0x1p-8);
+    p[4] = (float)(s2 * 0x1p-16);
+    p[5] = (float)(s3 * 0x1p-24);
+    p[6] = (float)(s4 * 0x1p-32);
 }
 // 2^e as a double for |e| < 1000
 __device__ __forceinline__ double oz_pow2(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
@@ -1172,7 +1174,7 @@ __global__ void oz_colexp_kernel(GemmDesc d, const double2 *__restrict__ B, cons
     }
 }
 
-// B' planes of the slots: per (slot, N tile, K tile) six planes of NR rows x 16 real K in the
+// B' planes of the slots: per (slot, N tile, K tile) seven planes of NR rows x 16 real K in the
 // canonical no-swizzle K-major layout (as bimage_kernel); thread = (slot, N tile, K tile, 4-column
 // group t, k pair kp, column nl)
 __global__ void oz_bimage_kernel(GemmDesc d, const double2 *__restrict__ B, const i64 *__restrict__ bsrc, const int *__restrict__ colexp,
@@ -1236,12 +1238,13 @@ __device__ __forceinline__ void dw_add(float &hi, float &lo, float vh, float vl)
 namespace {
 
 // FP64-accurate complex GEMM (see above). NR = 2 BNc real columns (32 or 64); TMEM holds
-// T0 / T1 / T of two chunk buffers at columns q * NR, q = 3 * buffer + accumulator.
+// T0 / T1 / T2 / T of two chunk buffers at columns q * NR, q = 4 * buffer + accumulator.
 template <int NR>
 __global__ void __launch_bounds__(TMA_THREADS, 1)
     tc_zgemm_oz_kernel(GemmDesc d, const __grid_constant__ CUtensorMap m0_, const __grid_constant__ CUtensorMap m1_,
                        const __grid_constant__ CUtensorMap m2_, const __grid_constant__ CUtensorMap m3_,
                        const __grid_constant__ CUtensorMap m4_, const __grid_constant__ CUtensorMap m5_,
+                       const __grid_constant__ CUtensorMap m6_,
                        const i64 *__restrict__ rowA, const int *__restrict__ rowexp, i64 arows, const i64 *__restrict__ bslot,
                        const float *__restrict__ img, const int *__restrict__ colexp, double2 *__restrict__ C, int S, int *err) {
     constexpr int BNc = NR / 2;
@@ -1294,7 +1297,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            const CUtensorMap *maps[OZ_PLANES] = {&m0_, &m1_, &m2_, &m3_, &m4_, &m5_};
+            const CUtensorMap *maps[OZ_PLANES] = {&m0_, &m1_, &m2_, &m3_, &m4_, &m5_, &m6_};
             int issued = 0;
             for (int kt = 0; kt < total; ++kt) {
                 const int s = kt % S;
@@ -1320,10 +1323,11 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t idesc = make_idesc(NR);
-            // (A plane, B plane, accumulator) of the 15 products
-            const int pa[15] = {0, 0, 1, 0, 0, 0, 2, 2, 2, 3, 3, 3, 4, 4, 5};
-            const int pb[15] = {0, 1, 0, 3, 4, 5, 2, 3, 4, 0, 2, 3, 0, 2, 0};
-            const int pc[15] = {0, 1, 1, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2};
+            // (A plane, B plane, accumulator) of the 15 products: T0 = s0 t0; T1 = s0 t1 + s1 t0;
+            // T2 = s0 t2 + s1 t1 + s2 t0; T = the nine scaled products with i + j = 3, 4
+            const int pa[15] = {0, 0, 1, 0, 1, 2, 0, 3, 4, 5, 0, 3, 4, 5, 6};
+            const int pb[15] = {0, 1, 0, 2, 1, 0, 5, 4, 3, 0, 6, 5, 4, 3, 0};
+            const int pc[15] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3, 3, 3, 3, 3, 3};
             int issued = 0, c = -1;
             for (int kt = 0; kt < total; ++kt) {
                 const int s = kt % S;
@@ -1345,7 +1349,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t sa = smem_u32(base + s * stage_bytes), sb = sa + OZ_PLANES * a_bytes;
-                const uint32_t tacc = tmem + (uint32_t)((c & 1) * 3 * NR);
+                const uint32_t tacc = tmem + (uint32_t)((c & 1) * 4 * NR);
 #pragma unroll
                 for (int ks = 0; ks < (2 * BKC3) / 8; ++ks) {
 #pragma unroll
@@ -1353,7 +1357,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
                         const uint64_t da = make_desc_sw64(sa + pa[q] * a_bytes + ks * 32);
                         const uint64_t db = make_desc_k16(sb + pb[q] * b_plane + ks * 256);
                         // the first product into each accumulator of a chunk overwrites it
-                        const bool first = cstart && ks == 0 && (q == 0 || q == 1 || q == 3);
+                        const bool first = cstart && ks == 0 && (q == 0 || q == 1 || q == 3 || q == 6);
                         mma_tf32(tacc + (uint32_t)(pc[q] * NR), da, db, idesc, first ? 0u : 1u);
                     }
                 }
@@ -1392,10 +1396,10 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
             const i64 ya = rowA[br] + m;
             const int ea = ya < arows ? rowexp[ya] : 0;
             const int *ce = colexp + (i64)bslot[br] * d.N;
-            const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((c & 1) * 3 * NR);
+            const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((c & 1) * 4 * NR);
 #pragma unroll
             for (int c0 = 0; c0 < NR; c0 += 8) {
-                uint32_t v0[8], v1[8], v2[8];
+                uint32_t v0[8], v1[8], v2[8], v3[8];
                 asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                              : "=r"(v0[0]), "=r"(v0[1]), "=r"(v0[2]), "=r"(v0[3]), "=r"(v0[4]), "=r"(v0[5]), "=r"(v0[6]), "=r"(v0[7])
                              : "r"(tbase + (uint32_t)c0));
@@ -1405,18 +1409,23 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
                 asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                              : "=r"(v2[0]), "=r"(v2[1]), "=r"(v2[2]), "=r"(v2[3]), "=r"(v2[4]), "=r"(v2[5]), "=r"(v2[6]), "=r"(v2[7])
                              : "r"(tbase + (uint32_t)(2 * NR + c0)));
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                             : "=r"(v3[0]), "=r"(v3[1]), "=r"(v3[2]), "=r"(v3[3]), "=r"(v3[4]), "=r"(v3[5]), "=r"(v3[6]), "=r"(v3[7])
+                             : "r"(tbase + (uint32_t)(3 * NR + c0)));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int n = n0 + (c0 + j) / 2;
                     const int eb = n < d.N ? ce[n] : 0;
-                    // value in units of 2^-24: T0 2^8 + T1 + T 2^8 (T0 2^8 + T1 as an exact pair)
-                    float vh, vl;
-                    two_sum(__uint_as_float(v0[j]) * 256.f, __uint_as_float(v1[j]), vh, vl);
-                    vl = __fmaf_rn(__uint_as_float(v2[j]), 256.f, vl);
-                    // scale by 2^(ea + eb - 24): exact inside the FP32 range (below it the term is dropped,
+                    // value in units of 2^-32: T0 2^16 + T1 2^8 + T2 + T 2^16 as a double word
+                    float vh, vl, s2, e2;
+                    two_sum(__uint_as_float(v0[j]) * 65536.f, __uint_as_float(v1[j]) * 256.f, vh, vl);
+                    two_sum(vh, __uint_as_float(v2[j]), s2, e2);
+                    vh = s2;
+                    vl = __fadd_rn(__fadd_rn(vl, e2), __uint_as_float(v3[j]) * 65536.f);
+                    // scale by 2^(ea + eb - 32): exact inside the FP32 range (below it the term is dropped,
                     // above it the result becomes infinite, so that no wrong finite value is written)
-                    const int ex = ea + eb - 24 + 127;
+                    const int ex = ea + eb - 32 + 127;
                     const float sc = ex < 1 ? 0.f : (ex > 254 ? __int_as_float(0x7f800000) : __int_as_float(ex << 23));
                     dw_add(ah[c0 + j], al[c0 + j], vh * sc, vl * sc);
                 }
@@ -1462,11 +1471,11 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
 }  // namespace
 
 // ----------------------------------------------------------------------------- host side of the FP64-accurate path
-// Six planes and the row exponents of an intermediate, made on first use for one row length
+// Seven planes and the row exponents of an intermediate, made on first use for one row length
 // (the view its GEMMs use), only while the device keeps its reserve free afterwards.
 struct OzPlanes {
     i64 rs = 0, rows = 0;
-    DBuf<float2> planes;   // [6][n]
+    DBuf<float2> planes;   // [7][pstride]
     DBuf<int> rowexp;      // [rows]
     CUtensorMap maps[OZ_PLANES];
 };
@@ -1538,7 +1547,8 @@ static void launch_oz_cols(dim3 grid, size_t smem, cudaStream_t st, const GemmDe
                            const i64 *bslot, const float *img, const int *colexp, double2 *C, int S, int *err) {
     cudaFuncSetAttribute(tc_zgemm_oz_kernel<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     tc_zgemm_oz_kernel<NR><<<grid, TMA_THREADS, smem, st>>>(with_wait_limit(d), P->maps[0], P->maps[1], P->maps[2], P->maps[3],
-                                                           P->maps[4], P->maps[5], rowA, P->rowexp.p, P->rows, bslot, img, colexp, C,
+                                                           P->maps[4], P->maps[5], P->maps[6], rowA, P->rowexp.p, P->rows, bslot, img,
+                                                           colexp, C,
                                                            S, err);
 }
 
