@@ -92,7 +92,7 @@ def parse():
     ap.add_argument("--no-chosen", action="store_true", help="skip the chosen-form measurement")
     ap.add_argument("--chosen-prec", default="tf32x3", choices=["tf32x3", "fp32"],
                     help="inner sigma of the chosen form: tensor cores (3xTF32) or FP32 SIMT")
-    ap.add_argument("--refine", default="fp64", choices=["fp64", "fp64_tc"],
+    ap.add_argument("--refine", default="fp64_tc", choices=["fp64", "fp64_tc"],
                     help="true residual of the chosen form: FP64 SIMT sigma, or the FP64-accurate sliced tensor-core sigma")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -376,7 +376,9 @@ def gpu_arm(args):
     steps_grid = total_elems / elems_per_step
     form_names = {B.FP64: "plain fp64 (every step in FP64)",
                   B.TF32X3: ("chosen: tensor-core sigma (tcgen05 kind::tf32, operands split hi+lo, 3 MMAs, FP32 accumulate) "
-                             "inside FP64 refinement (FP64 Krylov basis, FP64 true residual)"),
+                             "inside FP64 refinement (FP64 Krylov basis; true residual with the "
+                             + ("FP64-accurate sliced tensor-core sigma, exact 8-bit slices, error ~2^-40 of sum|a||b|, "
+                                "FP64 SIMT where the sliced copy does not fit)" if args.refine == "fp64_tc" else "FP64 SIMT sigma)")),
                   B.FP32: "chosen: FP32 SIMT sigma inside FP64 refinement"}
     out = {"metric": METRIC, "value": round(value, 3), "unit": "G elements/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_v / args.steps, 3),
