@@ -24,6 +24,8 @@
 // for its issued copies and MMAs, frees its TMEM and returns without writing C.
 #include "ccgf_internal.h"
 #include <cuda.h>
+#include <atomic>
+#include <cstdio>
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -1524,6 +1526,11 @@ static const OzPlanes *oz_planes(ccgf_handle *h, int a_buf, i64 rs, cudaStream_t
     const unsigned g = (unsigned)std::min<i64>(rows, 152 * 8);
     oz_plane_kernel<<<g, 256, 0, st>>>(h->W[a_buf].p, rows, rs, P->planes.p, pstride, P->rowexp.p);
     h->launches++;
+    if (cudaGetLastError() != cudaSuccess) {
+        delete P;
+        O->refused[a_buf] = true;
+        return nullptr;
+    }
     cuuint64_t dims[2] = {(cuuint64_t)(2 * rs), (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)(2 * rs * sizeof(float))};
     cuuint32_t box[2] = {(cuuint32_t)(2 * BKC3), (cuuint32_t)BM};
@@ -1543,13 +1550,25 @@ static const OzPlanes *oz_planes(ccgf_handle *h, int a_buf, i64 rs, cudaStream_t
 }
 
 template <int NR>
-static void launch_oz_cols(dim3 grid, size_t smem, cudaStream_t st, const GemmDesc &d, const OzPlanes *P, const i64 *rowA,
-                           const i64 *bslot, const float *img, const int *colexp, double2 *C, int S, int *err) {
-    cudaFuncSetAttribute(tc_zgemm_oz_kernel<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+static cudaError_t launch_oz_cols(dim3 grid, size_t smem, cudaStream_t st, const GemmDesc &d, const OzPlanes *P, const i64 *rowA,
+                                  const i64 *bslot, const float *img, const int *colexp, double2 *C, int S, int *err) {
+    cudaError_t e = cudaFuncSetAttribute(tc_zgemm_oz_kernel<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     tc_zgemm_oz_kernel<NR><<<grid, TMA_THREADS, smem, st>>>(with_wait_limit(d), P->maps[0], P->maps[1], P->maps[2], P->maps[3],
                                                            P->maps[4], P->maps[5], P->maps[6], rowA, P->rowexp.p, P->rows, bslot, img,
                                                            colexp, C,
                                                            S, err);
+    return cudaGetLastError();
+}
+
+// a launch the sliced path could not make: the caller falls back to FP64 SIMT; the first few are
+// reported on stderr with the GEMM's shape (they indicate a shape this path does not handle)
+static int oz_launch_failed(const char *what, cudaError_t e, const GemmDesc &d, size_t smem) {
+    static std::atomic<int> reported{0};
+    if (reported.fetch_add(1) < 4)
+        fprintf(stderr, "ccgf: sliced FP64 GEMM not used (%s: %s; M %d N %d K %d nred %d batch %d smem %zu)\n", what,
+                cudaGetErrorString(e), d.M, d.N, d.K, d.nred, d.batch, smem);
+    return 0;
 }
 
 bool tc_zgemm_oz_supported(const GemmDesc &d) { return d.M > 0 && d.N > 0 && d.K > 0 && d.csA == 1 && (d.rsA % 2) == 0; }
@@ -1582,18 +1601,21 @@ int launch_tc_zgemm_oz(ccgf_handle *h, int a_buf, const GemmDesc &d, const i64 *
     if (S > OZ_MAX_STAGES) S = OZ_MAX_STAGES;
     if (S < 2) return 0;
     const size_t smem = S * stage + extra;
+    const dim3 grid((unsigned)ntiles, (unsigned)ceil_div(d.M, BM), (unsigned)d.batch);
+    if (grid.y > 65535 || grid.z > 65535) return 0;
     {
+        if (cudaPeekAtLastError() != cudaSuccess) return 0;   // an earlier error is left to its caller
         const i64 g = ceil_div(ncol * 32, 256);
         oz_colexp_kernel<<<(unsigned)(g > 152 * 16 ? 152 * 16 : g), 256, 0, st>>>(d, B, bsrc, nslots, O->colexp.p);
         const i64 total = (i64)nslots * ntiles * ktiles * (BNc / 4) * 16;
         const i64 g2 = ceil_div(total, 256);
         oz_bimage_kernel<<<(unsigned)(g2 > 152 * 32 ? 152 * 32 : g2), 256, 0, st>>>(d, B, bsrc, O->colexp.p, nslots, BNc, ntiles,
                                                                                     ktiles, O->img.p);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return oz_launch_failed("B image", e, d, smem);
     }
-    const dim3 grid((unsigned)ntiles, (unsigned)ceil_div(d.M, BM), (unsigned)d.batch);
-    if (NR == 32)
-        launch_oz_cols<32>(grid, smem, st, d, P, rowA, bslot, O->img.p, O->colexp.p, C, S, err);
-    else
-        launch_oz_cols<64>(grid, smem, st, d, P, rowA, bslot, O->img.p, O->colexp.p, C, S, err);
+    const cudaError_t e = NR == 32 ? launch_oz_cols<32>(grid, smem, st, d, P, rowA, bslot, O->img.p, O->colexp.p, C, S, err)
+                                   : launch_oz_cols<64>(grid, smem, st, d, P, rowA, bslot, O->img.p, O->colexp.p, C, S, err);
+    if (e != cudaSuccess) return oz_launch_failed("GEMM", e, d, smem);
     return 3;
 }
