@@ -92,8 +92,9 @@ def parse():
     ap.add_argument("--no-chosen", action="store_true", help="skip the chosen-form measurement")
     ap.add_argument("--chosen-prec", default="tf32x3", choices=["tf32x3", "fp32"],
                     help="inner sigma of the chosen form: tensor cores (3xTF32) or FP32 SIMT")
-    ap.add_argument("--refine", default="fp64_tc", choices=["fp64", "fp64_tc"],
-                    help="true residual of the chosen form: FP64 SIMT sigma, or the FP64-accurate sliced tensor-core sigma")
+    ap.add_argument("--refine", default="auto", choices=["auto", "fp64", "fp64_tc"],
+                    help="true residual of the chosen form: FP64 SIMT sigma, or the FP64-accurate sliced tensor-core "
+                         "sigma (auto: the workload's setting)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -193,10 +194,13 @@ class ClockSampler:
 #   one_k: one (k-point, frequency) pair, every orbital (nmo^2 G elements per step), for meshes where a
 #          step over all k would take minutes
 PROFILE = {
-    "gamma_ip_o4v12": dict(form="fp64", per_step="all_k", sectors="ip"),
-    "si_k222_o4v22": dict(form="fp64", per_step="all_k", sectors="ipea"),
-    "si_k333_o4v30": dict(form="tf32x3", per_step="one_k", sectors="ipea"),
-    "zno_k222_o18v60": dict(form="tf32x3", per_step="one_k", sectors="ipea"),
+    # refine: the chosen form's true-residual sigma. The sliced FP64-accurate tensor-core sigma where
+    # its copies of the intermediates fit; on the 3x3x3 and ZnO-like meshes the ladder's would not,
+    # the other sliced copies then only take memory from the batch, and FP64 SIMT is used
+    "gamma_ip_o4v12": dict(form="fp64", per_step="all_k", sectors="ip", refine="fp64_tc"),
+    "si_k222_o4v22": dict(form="fp64", per_step="all_k", sectors="ipea", refine="fp64_tc"),
+    "si_k333_o4v30": dict(form="tf32x3", per_step="one_k", sectors="ipea", refine="fp64"),
+    "zno_k222_o18v60": dict(form="tf32x3", per_step="one_k", sectors="ipea", refine="fp64"),
 }
 
 
@@ -238,6 +242,8 @@ def gpu_arm(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     prof_cfg = PROFILE[args.workload]
+    if args.refine == "auto":
+        args.refine = prof_cfg["refine"]
     s = make_workload(args.workload)
     nk, N = s.nk, s.nmo
     nomega = len(s.omega)

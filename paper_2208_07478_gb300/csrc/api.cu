@@ -49,6 +49,7 @@ void destroy(ccgf_handle *h) {
     dfree(h->abi_y);
     tc_free(h);
     oz_free(h);
+    vcache_free(h);
     delete h;
 }
 

@@ -277,6 +277,13 @@ struct ccgf_handle {
         double2 *X = nullptr;   // [D][nmo * nw]
     } mor_cap;
     bool ws_capturing = false;
+    // right-hand sides b_p and left vectors e_q of solve_gf per (sector, K) (they do not depend on the
+    // frequency), kept while their total stays under a small share of device memory
+    struct VecCache {
+        DBuf<double2> Bq, E;
+    };
+    std::vector<VecCache *> vcache;
+    size_t vcache_bytes = 0;
     // bound of every tensor-core device wait (from ccgf_options::device_wait_timeout_ms)
     unsigned long long wait_ns = 1000000000ull;
     // three zero offsets on this handle's device (single-block GEMM / permute launches)
@@ -300,6 +307,7 @@ ccgf_status sigma_apply(ccgf_handle *h, int sector, int K, int nv, const double2
                         ccgf_precision prec, cudaStream_t st);
 void free_plans(ccgf_handle *h);
 void release_caches(ccgf_handle *h);   // FP32 / TF32 copies, scratch arenas (rebuilt on demand)
+void vcache_free(ccgf_handle *h);      // solve.cu: cached right-hand sides and left vectors
 void set_autotune(bool on);
 int plan_step_choice(const ccgf_handle *h, int sector, int K, int step, int prec_index);
 // reads and clears the tensor-core error flag (synchronises st); CCGF_ERR_TIMEOUT when it was set

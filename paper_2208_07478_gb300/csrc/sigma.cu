@@ -777,49 +777,54 @@ SigmaPlan *build_plan_ip(const ccgf_handle *h, int K, int nv) {
 // ---------------------------------------------------------------- Fov terms
 // IP: y1[i] += sum_{km,m,e} f_me (2 x2[K,km][i,m,e] - x2[km,K][m,i,e])
 // EA: y1[a] += sum_{km,m,e} f_me (2 x2[km,K][m,a,e] - x2[km,km][m,e,a])
+// One block per output row p: thread (c0 = tid % cw, g = tid / cw) sums the terms t = g, g + G, ...
+// of column c = c0 (+ cw, ...), the G partial sums are added in a fixed order (the few-row
+// reduction has nk o v terms, too long for one thread per output).
 template <typename T, typename R>
-__global__ void fov_kernel(int sector, int K, int nk, int o, int v, int nv, const T *__restrict__ Fov,
+__global__ void fov_kernel(int sector, int K, int nk, int o, int v, int nv, int cw, const T *__restrict__ Fov,
                            const T *__restrict__ x, T *__restrict__ y) {
-    const int nrow = sector == CCGF_SECTOR_IP ? o : v;
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid >= nrow * nv) return;
-    const int p = tid / nv, c = tid % nv;
-    R ax = 0, ay = 0;
-    if (sector == CCGF_SECTOR_IP) {
-        const i64 S2 = (i64)o * o * v;
-        for (int kmm = 0; kmm < nk; ++kmm) {
-            const T *a = x + (o + ((i64)K * nk + kmm) * S2) * nv;
-            const T *b = x + (o + ((i64)kmm * nk + K) * S2) * nv;
-            for (int m = 0; m < o; ++m)
-                for (int e = 0; e < v; ++e) {
-                    T f = Fov[((i64)kmm * o + m) * v + e];
-                    T u = a[((i64)(p * o + m) * v + e) * nv + c];
-                    T w = b[((i64)(m * o + p) * v + e) * nv + c];
-                    R zx = 2 * u.x - w.x, zy = 2 * u.y - w.y;
-                    ax += f.x * zx - f.y * zy;
-                    ay += f.x * zy + f.y * zx;
+    __shared__ R red[2][256];
+    const int p = blockIdx.x;
+    const int c0 = (int)threadIdx.x % cw, g = (int)threadIdx.x / cw, G = (int)blockDim.x / cw;
+    const int ov = o * v, nterm = nk * ov;
+    for (int cb = 0; cb < nv; cb += cw) {
+        const int c = cb + c0;
+        R ax = 0, ay = 0;
+        if (c < nv) {
+            for (int t = g; t < nterm; t += G) {
+                const int kmm = t / ov, m = (t / v) % o, e = t % v;
+                const T f = Fov[((i64)kmm * o + m) * v + e];
+                T u, w;
+                if (sector == CCGF_SECTOR_IP) {
+                    const i64 S2 = (i64)o * o * v;
+                    u = x[(o + ((i64)K * nk + kmm) * S2 + (i64)(p * o + m) * v + e) * nv + c];
+                    w = x[(o + ((i64)kmm * nk + K) * S2 + (i64)(m * o + p) * v + e) * nv + c];
+                } else {
+                    const i64 S2 = (i64)o * v * v;
+                    u = x[(v + ((i64)kmm * nk + K) * S2 + (i64)(m * v + p) * v + e) * nv + c];
+                    w = x[(v + ((i64)kmm * nk + kmm) * S2 + (i64)(m * v + e) * v + p) * nv + c];
                 }
+                const R zx = 2 * u.x - w.x, zy = 2 * u.y - w.y;
+                ax += f.x * zx - f.y * zy;
+                ay += f.x * zy + f.y * zx;
+            }
         }
-    } else {
-        const i64 S2 = (i64)o * v * v;
-        for (int kmm = 0; kmm < nk; ++kmm) {
-            const T *a = x + (v + ((i64)kmm * nk + K) * S2) * nv;
-            const T *b = x + (v + ((i64)kmm * nk + kmm) * S2) * nv;
-            for (int m = 0; m < o; ++m)
-                for (int e = 0; e < v; ++e) {
-                    T f = Fov[((i64)kmm * o + m) * v + e];
-                    T u = a[((i64)(m * v + p) * v + e) * nv + c];
-                    T w = b[((i64)(m * v + e) * v + p) * nv + c];
-                    R zx = 2 * u.x - w.x, zy = 2 * u.y - w.y;
-                    ax += f.x * zx - f.y * zy;
-                    ay += f.x * zy + f.y * zx;
-                }
+        red[0][threadIdx.x] = ax;
+        red[1][threadIdx.x] = ay;
+        __syncthreads();
+        if (g == 0 && c < nv) {
+            R sx = 0, sy = 0;
+            for (int q = 0; q < G; ++q) {
+                sx += red[0][q * cw + c0];
+                sy += red[1][q * cw + c0];
+            }
+            T out = y[(i64)p * nv + c];
+            out.x += sx;
+            out.y += sy;
+            y[(i64)p * nv + c] = out;
         }
+        __syncthreads();
     }
-    T out = y[(i64)p * nv + c];
-    out.x += ax;
-    out.y += ay;
-    y[(i64)p * nv + c] = out;
 }
 
 // EA ladder, pair-symmetric form. Pair representatives reps[s][beta] = (ke * v + e) * v + f,
@@ -1166,8 +1171,8 @@ void run_plan(ccgf_handle *h, SigmaPlan *P, const double2 *x, double2 *y, cudaSt
             const int sector = s.kind == STEP_FOV_IP ? CCGF_SECTOR_IP : CCGF_SECTOR_EA;
             const int nrow = sector == CCGF_SECTOR_IP ? h->o : h->v;
             const T *F = f64 ? (const T *)h->W[BUF_FOV].p : (const T *)h->Wf[BUF_FOV].p;
-            fov_kernel<T, R><<<(unsigned)ceil_div((i64)nrow * P->nv, 128), 128, 0, st>>>(
-                sector, P->K, h->nk, h->o, h->v, P->nv, F, scr + P->seg[SEG_X], yout);
+            fov_kernel<T, R><<<(unsigned)nrow, (unsigned)((256 / std::min(P->nv, 256)) * std::min(P->nv, 256)), 0, st>>>(
+                sector, P->K, h->nk, h->o, h->v, P->nv, std::min(P->nv, 256), F, scr + P->seg[SEG_X], yout);
             h->launches++;
         }
     }
@@ -1301,6 +1306,7 @@ int plan_step_choice(const ccgf_handle *h, int sector, int K, int step, int pi) 
 void release_caches(ccgf_handle *h) {
     tc_free(h);
     oz_free(h);
+    vcache_free(h);
     for (int b = 0; b < NBUF; ++b) dfree(h->Wf[b]);
     h->fp32_done = false;
     dfree(h->scratch);

@@ -481,6 +481,14 @@ void mor_capture_columns(ccgf_handle *h, const double2 *X, i64 D, int nv, int p0
     h->launches++;
 }
 
+void vcache_free(ccgf_handle *h) {
+    for (auto *&vc : h->vcache) {
+        delete vc;
+        vc = nullptr;
+    }
+    h->vcache_bytes = 0;
+}
+
 ccgf_status diag_estimate_device(ccgf_handle *h, int sector, int K, double *d, cudaStream_t st) {
     const i64 D = sector == CCGF_SECTOR_IP ? h->dim_ip : h->dim_ea;
     diag_kernel<<<g1(D), 256, 0, st>>>(sector, K, h->nk, h->o, h->v, h->kadd_d.p, h->ksub_d.p, h->W[BUF_FOO].p,
@@ -642,9 +650,31 @@ ccgf_status solve_gf(ccgf_handle *h, int sectors, int nomega, const double *omeg
             dfree(nunconv);
         };
         for (int K = kbeg; K < kend; ++K) {
-            for (int p = 0; p < N; ++p) {
-                CCGF_TRY(make_rhs(h, sector, K, p, Bq.p + p, N, st));
-                CCGF_TRY(make_left(h, sector, K, p, E.p + (i64)p * D, 1, st));
+            const size_t vbytes = sizeof(double2) * (size_t)D * N;
+            const int vkey = (sector - 1) * nk + K;
+            if (h->vcache.empty()) h->vcache.assign(2 * nk, nullptr);
+            if (ccgf_handle::VecCache *vc = h->vcache[vkey]) {
+                CCGF_CUDA_TRY(cudaMemcpyAsync(Bq.p, vc->Bq.p, vbytes, cudaMemcpyDeviceToDevice, st));
+                CCGF_CUDA_TRY(cudaMemcpyAsync(E.p, vc->E.p, vbytes, cudaMemcpyDeviceToDevice, st));
+            } else {
+                for (int p = 0; p < N; ++p) {
+                    CCGF_TRY(make_rhs(h, sector, K, p, Bq.p + p, N, st));
+                    CCGF_TRY(make_left(h, sector, K, p, E.p + (i64)p * D, 1, st));
+                }
+                // keep them for later solves while the cache stays below 2 GB and 2 % of the device
+                size_t fr = 0, tot = 0;
+                if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && h->vcache_bytes + 2 * vbytes <= std::min<size_t>((size_t)2 << 30, tot / 50) &&
+                    fr > 2 * vbytes + ((size_t)4 << 30)) {
+                    auto *nvc = new ccgf_handle::VecCache();
+                    if (dalloc(nvc->Bq, D * N) == CCGF_OK && dalloc(nvc->E, D * N) == CCGF_OK) {
+                        CCGF_CUDA_TRY(cudaMemcpyAsync(nvc->Bq.p, Bq.p, vbytes, cudaMemcpyDeviceToDevice, st));
+                        CCGF_CUDA_TRY(cudaMemcpyAsync(nvc->E.p, E.p, vbytes, cudaMemcpyDeviceToDevice, st));
+                        h->vcache[vkey] = nvc;
+                        h->vcache_bytes += 2 * vbytes;
+                    } else {
+                        delete nvc;
+                    }
+                }
             }
             diag_kernel<<<g1(D), 256, 0, st>>>(sector, K, nk, o, v, h->kadd_d.p, h->ksub_d.p, h->W[BUF_FOO].p, h->W[BUF_FVV].p, dvec.p, D);
             h->launches++;

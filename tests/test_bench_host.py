@@ -83,3 +83,9 @@ def test_vector_roofline_names_the_binding_resource():
     assert r["bound"] == "alu"
     assert abs(r["frac_of_bound"] - (1e9 / (bench.FP64_PEAK_TFLOPS * 1e12)) / 1e-3) < 1e-4
     assert bench.vector_roofline({"vector_ms": 0.0})["gbs"] is None
+
+
+def test_every_workload_names_its_refinement():
+    for name, cfg in bench.PROFILE.items():
+        assert cfg["refine"] in ("fp64", "fp64_tc"), name
+        assert cfg["form"] in ("fp64", "tf32x3", "fp32"), name
