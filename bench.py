@@ -383,7 +383,7 @@ def gpu_arm(args):
     form_names = {B.FP64: "plain fp64 (every step in FP64)",
                   B.TF32X3: ("chosen: tensor-core sigma (tcgen05 kind::tf32, operands split hi+lo, 3 MMAs, FP32 accumulate) "
                              "inside FP64 refinement (FP64 Krylov basis; true residual with the "
-                             + ("FP64-accurate sliced tensor-core sigma, exact 8-bit slices, error ~2^-40 of sum|a||b|, "
+                             + ("FP64-accurate sliced tensor-core sigma, exact 8-bit slices, error ~2^-41 of n max|a| max|b|, "
                                 "FP64 SIMT where the sliced copy does not fit)" if args.refine == "fp64_tc" else "FP64 SIMT sigma)")),
                   B.FP32: "chosen: FP32 SIMT sigma inside FP64 refinement"}
     out = {"metric": METRIC, "value": round(value, 3), "unit": "G elements/s", "n_gpus": world,

@@ -66,7 +66,7 @@ typedef enum {
                             sums below 2^24 are exact in tcgen05.mma.kind::tf32, so the product
                             terms down to 2^-32 of the leading one are formed exactly, those down
                             to 2^-40 with FP32 rounding far below that, and smaller ones dropped
-                            (error ~2^-40 of sum |a||b|). Partial sums are drained into double-word
+                            (error ~2^-41 of n max|a| max|b|). Partial sums are drained into double-word
                             FP32 accumulators and the result written in FP64. The other
                             contractions, and those whose sliced copy does not fit in device memory
                             (3.5 x the FP64 intermediate), run in FP64 SIMT. Treated as FP64 by the
@@ -293,9 +293,8 @@ const char *ccgf_sigma_step_name(const ccgf_handle *h, int sector, int kshift, i
  * whose device memory is already fully reserved). All scratch lives in one static
  * device array of 32 MiB per device (held until the process exits); a (dim_ip, nvec)
  * that does not fit returns CCGF_ERR_INVALID_ARG with the size it would need. The
- * first call on a device looks up the array's address (make it before any stream
- * capture). Calls share the array: calls whose kernels overlap on the GPU race, so
- * order them. x, y: device complex [nvec][dim_ip], as ccgf_sigma_ip; stream-ordered,
+ * first call on a device looks up the array's address. Calls share the array: calls
+ * whose kernels overlap on the GPU race, so order them. x, y: device complex [nvec][dim_ip], as ccgf_sigma_ip; stream-ordered,
  * does not synchronise. */
 ccgf_status ccgf_sigma_ip_noalloc(ccgf_handle *h, int kshift, long long nvec, const double *x,
                                   double *y, void *stream);

@@ -19,8 +19,7 @@
 //     elements). A call whose (dimension, nvec) needs more returns
 //     CCGF_ERR_INVALID_ARG and says how much it would need.
 //   - The first call on each device looks up the array's device address with
-//     cudaGetSymbolAddress (with that device current) and caches it; make that first
-//     call before any stream capture on that device.
+//     cudaGetSymbolAddress (with that device current) and caches it.
 //   - All calls share the one array and leave their contents in it. Every scratch
 //     element is written before it is read within a call, so nothing has to start
 //     at zero; but calls whose kernels overlap on the GPU (different streams, or

@@ -1094,7 +1094,8 @@ void launch_wait_selftest(double limit_ms, int *err, cudaStream_t st) {
 // A as seven stored planes (s0, s1, s2 and s1 2^-8, s2 2^-16, s3 2^-24, s4 2^-32) of the FP64
 // intermediate with one exponent per stored row, by TMA; B as the same seven planes of the
 // 2x2-embedded B' tile with one exponent per (block, column), written by oz_bimage_kernel and fetched
-// by one cp.async.bulk per stage. Error ~2^-40 of sum |a||b|.
+// by one cp.async.bulk per stage. Error ~2^-41 of n max|a| max|b| (largest magnitudes of the row of A
+// and the column of B).
 namespace {
 
 constexpr int OZ_PLANES = 7;
