@@ -1,24 +1,23 @@
 """Benchmark of the periodic CCGF hot path on GB300.
 
-Workload (default): the Si-like 2x2x2 k-mesh system, nocc = 4, nvir = 22 per k,
-Naux = 96, 64 frequencies in [-0.8, 0.8] Ha, eta = 0.005 Ha, both sectors,
-synthetic seeded inputs. One step = one frequency point: for all 8 k-points
-and all 26 orbitals, the removal (IP) and addition (EA) shifted systems are
-solved by batched GMRES to relative residual 1e-6 and contracted into
-G_pq(k, w) (8 * 26^2 = 5408 complex elements per step). Successive steps take
-successive points of the frequency grid. The timed region also holds one build
-of the similarity-transformed Hamiltonian blocks from device-resident inputs,
-amortised over the K steps.
+Workload (default): the Si-like 3x3x3 k-mesh system (nk = 27, nocc = 4, nvir = 30 per k,
+Naux = 96, 128 frequencies in [-0.8, 0.8] Ha, eta = 0.005 Ha), synthetic seeded inputs. One step
+= one (k-point, frequency) pair: the removal (IP) and addition (EA) shifted systems of all 34
+orbitals are solved by batched GMRES to relative residual 1e-6 and contracted into G_pq(k, w)
+(34^2 = 1156 complex elements per step); successive steps take successive (k, w) pairs. The
+build of the similarity-transformed Hamiltonian blocks is timed apart (a one-time cost).
+`value` there is the chosen form: inner sigma on the tensor cores (3xTF32) inside refinement
+whose true residual is computed in FP64; the plain FP64 form is timed on an equal-work slice.
 
-`value` is the plain FP64 form (every step in FP64). The chosen form (inner
-sigma on the tensor cores with 3xTF32 operands, inside FP64 refinement, same
-FP64-verified residual target) is reported beside it with its ratio to the
-plain form.
+--workload si_k222_o4v22: the Si 2x2x2 shape (nk = 8, nocc = 4, nvir = 22, 64 frequencies);
+one step = one frequency for all 8 k-points. `value` there is the plain FP64 form (every step in
+FP64), the chosen form (true residual from the FP64-accurate sliced tensor-core sigma) is timed
+on the same steps beside it.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference] [--workload NAME]
 
-Under torchrun every rank solves its own frequency points (no data-path
-collective); rank 0 prints one JSON line.
+Under torchrun every rank solves its own (k, w) points (no data-path collective); rank 0
+prints one JSON line.
 """
 import argparse
 import json
@@ -85,7 +84,8 @@ def measured_peaks():
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: the workload's, about a minute of timed work)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
@@ -197,10 +197,11 @@ PROFILE = {
     # refine: the chosen form's true-residual sigma. The sliced FP64-accurate tensor-core sigma where
     # its copies of the intermediates fit; on the 3x3x3 and ZnO-like meshes the ladder's would not,
     # the other sliced copies then only take memory from the batch, and FP64 SIMT is used
-    "gamma_ip_o4v12": dict(form="fp64", per_step="all_k", sectors="ip", refine="fp64_tc"),
-    "si_k222_o4v22": dict(form="fp64", per_step="all_k", sectors="ipea", refine="fp64_tc"),
-    "si_k333_o4v30": dict(form="tf32x3", per_step="one_k", sectors="ipea", refine="fp64"),
-    "zno_k222_o18v60": dict(form="tf32x3", per_step="one_k", sectors="ipea", refine="fp64"),
+    # steps: the default number of timed steps (about a minute of timed work)
+    "gamma_ip_o4v12": dict(form="fp64", per_step="all_k", sectors="ip", refine="fp64_tc", steps=4),
+    "si_k222_o4v22": dict(form="fp64", per_step="all_k", sectors="ipea", refine="fp64_tc", steps=4),
+    "si_k333_o4v30": dict(form="tf32x3", per_step="one_k", sectors="ipea", refine="fp64", steps=1),
+    "zno_k222_o18v60": dict(form="tf32x3", per_step="one_k", sectors="ipea", refine="fp64", steps=1),
 }
 
 
@@ -671,6 +672,8 @@ def reference_arm(args):
 
 def main():
     args = parse()
+    if args.steps is None:
+        args.steps = PROFILE[args.workload]["steps"]
     if args.impl == "reference":
         reference_arm(args)
     else:

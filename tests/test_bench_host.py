@@ -89,3 +89,10 @@ def test_every_workload_names_its_refinement():
     for name, cfg in bench.PROFILE.items():
         assert cfg["refine"] in ("fp64", "fp64_tc"), name
         assert cfg["form"] in ("fp64", "tf32x3", "fp32"), name
+
+
+def test_default_steps_come_from_the_workload(monkeypatch):
+    monkeypatch.setattr("sys.argv", ["bench.py"])
+    a = bench.parse()
+    assert a.steps is None and a.workload == bench.WORKLOAD
+    assert bench.PROFILE[bench.WORKLOAD]["steps"] >= 1
