@@ -27,9 +27,11 @@
  *     the stream only where stated: ccgf_solve_gf reads the convergence flags
  *     once per Arnoldi step; a sigma call synchronises only when it first meets
  *     a new vector count or momentum (plan and workspace set-up, which may
- *     allocate) and, with CCGF_TF32X3, once at its end to read the tensor-core
- *     error flag. Repeated FP64 / FP32 sigma calls of one shape allocate
- *     nothing and do not synchronise.
+ *     allocate) and, with CCGF_TF32X3 or CCGF_FP64_TC, once at its end to read
+ *     the tensor-core error flag. Repeated FP64 / FP32 sigma calls of one shape
+ *     allocate nothing and do not synchronise. Copies kept only for speed (FP32
+ *     and sliced copies of the intermediates, cached right-hand sides and left
+ *     vectors) are released when a call needs their memory and made again later.
  *   - Errors are returned as status codes; nothing aborts, throws or traps.
  *     ccgf_last_error() gives a message for the last failing call on this
  *     thread. One handle per host thread.
